@@ -211,8 +211,11 @@ def steady_state_iterative(H, c_ops, method: str = "bicgstab", precond: str = "i
 
     The Krylov stop is an absolute residual bound that starts at tol / 2 and is
     tightened tenfold (restarting from the current iterate) whenever the
-    acceptance test ||L rho||_2 <= tol fails. For inverse power each inner
-    solve uses tol / 10 relative to ||x_k|| = 1 (section "Iterative solvers").
+    acceptance test ||L rho||_2 <= tol fails; a BiCGSTAB breakdown after at
+    least one iteration restarts from the current iterate with a fresh shadow
+    residual (at most 8 passes, 1000 iterations in all). For inverse power
+    each inner solve uses tol / 10 relative to ||x_k|| = 1 (section
+    "Iterative solvers").
     """
     d = H.shape[0]
     n = d * d
@@ -286,10 +289,12 @@ def steady_state_iterative(H, c_ops, method: str = "bicgstab", precond: str = "i
         if lr <= tol:
             status = OK
             break
-        if res.status != OK or total >= maxiter:
-            status = res.status
+        if total >= maxiter or res.status == NOT_CONVERGED or (res.status == BREAKDOWN and res.iters == 0):
+            status = res.status if res.status != OK else NOT_CONVERGED
             break
-        inner /= 10.0
+        if res.status == OK:
+            inner /= 10.0
+        # BREAKDOWN after progress: restart from the current iterate with a new shadow residual
     return SteadyResult(_unvec_norm(x, d), status, total, 1, lr, perm, wv)
 
 

@@ -111,9 +111,11 @@ def modified_liouvillian(L, d: int, w: float):
 
 
 def default_weight(L) -> float:
-    """The weighting factor w read as the mean modulus of L's diagonal."""
+    """The weighting factor w read as the mean modulus of L's diagonal (1 when
+    that mean is zero, since any positive w gives the same solution)."""
     diag = L.diagonal() if sp.issparse(L) else np.diag(L)
-    return float(np.mean(np.abs(diag)))
+    w = float(np.mean(np.abs(diag)))
+    return w if w > 0.0 else 1.0
 
 
 def shifted_liouvillian(L, sigma: float = 1e-15):
