@@ -1,0 +1,380 @@
+"""Benchmark: steady-state solves/s of the driven dissipative Jaynes-Cummings
+workload (cavity cutoff 40 x two-level atom, Hilbert dimension 80, a
+6400 x 6400 complex128 Liouvillian), at ||L rho||_2 <= 1e-10 in FP64.
+
+One step = one batch of S systems (seeds rank*S .. rank*S+S-1, drive
+E ~ U[0.2, 1.5]) taken through the whole path on the GPU: Kronecker assembly
+of L, trace row of Eq. (linear), RCM ordering, incomplete LU, preconditioned
+Krylov iteration, acceptance test and trace-normalised rho.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line (rank 0).  `value` is timed with CUDA events on the
+solver's stream with H and C_k already in device memory and rho written to
+device memory; `e2e` repeats the measurement through the same public call
+with host inputs and a host rho (the copies are inside the timed region).
+L2 is flushed (a 256 MiB write) between timed steps, outside the events.
+The reference arm (--impl reference) times the CPU oracle (dense FP64 LU of
+the trace-row system) on the host cores on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "steady-state solves/s at ||L rho||<=1e-10 (FP64)"
+UNIT = "solves/s"
+TOL = 1e-10
+BATCH = 32
+JC_N = 40
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _systems(rank: int):
+    from workloads import jaynes_cummings_rwa
+    return [jaynes_cummings_rwa(seed=rank * BATCH + s, N=JC_N) for s in range(BATCH)]
+
+
+# --------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    import paper_1504_06768_gb300 as ss
+    from paper_1504_06768_gb300 import _binding as B
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib = B.load()
+    stream = torch.cuda.current_stream()
+    ctx = ss.Context(local, stream)
+    systems = _systems(rank)
+    d = systems[0].d
+    precond = args.precond
+
+    # device-resident CSR inputs (H and C_k) and outputs
+    def dev_view(m):
+        import scipy.sparse as sp
+        m = sp.csr_matrix(m)
+        rp = torch.as_tensor(m.indptr.astype(np.int32), device="cuda")
+        col = torch.as_tensor(m.indices.astype(np.int32), device="cuda")
+        val = torch.as_tensor(m.data.astype(np.complex128), device="cuda")
+        v = B.CsrView(m.shape[0], m.shape[1], m.nnz, rp.data_ptr(), col.data_ptr(), val.data_ptr(), 1)
+        return v, (rp, col, val)
+
+    dev_inputs = []
+    keep = []
+    for s in systems:
+        hv, k1 = dev_view(s.H)
+        cvs = [dev_view(c) for c in s.c_ops]
+        arr = (B.CsrView * len(cvs))(*[c[0] for c in cvs])
+        keep.append((k1, [c[1] for c in cvs], arr))
+        dev_inputs.append((hv, arr, len(cvs)))
+    host_inputs = [(ss._CsrHost(s.H), [ss._CsrHost(c) for c in s.c_ops]) for s in systems]
+    host_arrays = [(hv, (B.CsrView * len(cs))(*[c.view for c in cs]), len(cs)) for hv, cs in host_inputs]
+    rho_dev = torch.empty((BATCH, d * d), dtype=torch.complex128, device="cuda")
+    rho_host = torch.empty((BATCH, d * d), dtype=torch.complex128).pin_memory()
+    opt = B.Options()
+    lib.ss_options_default(C.byref(opt))
+    opt.method = B.METHODS[args.method]
+    opt.precond = B.PRECONDS[precond]
+    opt.tol = TOL
+    info = B.Info()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    infos = []
+
+    def step(host=False):
+        for k in range(BATCH):
+            if host:
+                hv, arr, nc = host_arrays[k]
+                st = lib.steady_state(ctx.handle, C.byref(hv.view), nc, arr, C.byref(opt),
+                                      C.c_void_p(rho_host[k].data_ptr()), 0, C.byref(info))
+            else:
+                hv, arr, nc = dev_inputs[k]
+                st = lib.steady_state(ctx.handle, C.byref(hv), nc, arr, C.byref(opt),
+                                      C.c_void_p(rho_dev[k].data_ptr()), 1, C.byref(info))
+            if st != 0:
+                raise RuntimeError(f"steady_state failed: {B.STATUS_NAMES.get(st)} "
+                                   f"{lib.ss_last_error(ctx.handle).decode()}")
+            infos.append(info.as_dict())
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(n_steps, host=False, profile=False):
+        times = []
+        barrier()
+        for _ in range(n_steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(host)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        barrier()
+        return times
+
+    for _ in range(args.warmup):
+        step()
+    infos.clear()
+    lib.ss_profile_enable(ctx.handle, 1)
+    for kind in range(3):
+        lib.ss_profile_read(ctx.handle, kind, None, None)
+    with ClockSampler(local) as clk:
+        times = timed(args.steps)
+    lib.ss_profile_enable(ctx.handle, 0)
+    prof = {}
+    for kind, name in enumerate(["spmv", "trsv_lower", "trsv_upper"]):
+        cnt, ms = C.c_int64(), C.c_double()
+        lib.ss_profile_read(ctx.handle, kind, C.byref(cnt), C.byref(ms))
+        prof[name] = (cnt.value, ms.value)
+    step_infos = list(infos)
+    total_ms = sum(times)
+    ms_step = total_ms / args.steps
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = ws * BATCH / (ms_step / 1000.0)
+
+    # end to end through the same call with host buffers
+    infos.clear()
+    e2e_times = timed(max(1, min(args.steps, 3)), host=True)
+    e2e_ms = sum(e2e_times) / len(e2e_times)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = sum(hv.rp.nbytes + hv.col.nbytes + hv.val.nbytes + sum(c.rp.nbytes + c.col.nbytes + c.val.nbytes
+                                                                  for c in cs) for hv, cs in host_inputs)
+    d2h = BATCH * d * d * 16
+
+    # roofline of the dominant kernel (largest share of the profiled device time)
+    n = d * d
+    nnz = step_infos[0]["nnz"]
+    nnzf = step_infos[0]["nnz_factors"]
+    bytes_per = {
+        # val 16 B + col 4 B per entry, row_ptr 4 B + y 16 B per row, x read once 16 B per row
+        "spmv": 20 * nnz + 36 * n,
+        # each solve reads about half of the factors' entries plus the diagonal position,
+        # order index, rhs and result per row, and the completion flag per dependency
+        "trsv_lower": 20 * (nnzf - n) // 2 + 44 * n,
+        "trsv_upper": 20 * ((nnzf - n) // 2 + n) + 60 * n,
+    }
+    dom = max(prof, key=lambda k: prof[k][1])
+    cnt, ms = prof[dom]
+    peak, peak_kind = _peaks()
+    achieved = bytes_per[dom] / ((ms / max(cnt, 1)) / 1000.0) / 1e9 if cnt else None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_source": peak_kind, "launches": cnt, "avg_launch_us": 1000.0 * ms / max(cnt, 1),
+                "bytes_per_launch": bytes_per[dom],
+                "kernel_share_of_step": {k: prof[k][1] / total_ms for k in prof}}
+    # traffic per launch from the committed ncu summary, when it matches this build
+    tr_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_file):
+        tr = json.load(open(tr_file))
+        if tr.get("kernel") == dom and tr.get("workload") == "jc40":
+            roofline["traffic"] = tr.get("bytes_per_launch")
+
+    launches_per_step = sum(prof[k][0] for k in prof) / args.steps
+    resid = max(i["resid_Lrho"] for i in step_infos)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+        "config": {"workload": "jc40: driven dissipative Jaynes-Cummings, cavity 40 x atom, n=6400, "
+                               f"{BATCH} seeds per step (E~U[0.2,1.5])",
+                   "method": args.method, "precond": precond, "ordering": "rcm", "tol": TOL,
+                   "batch_per_gpu": BATCH, "parallelism": f"replicas x{ws}",
+                   "l2": "flushed between timed steps (256 MiB write, outside the events)"},
+        "e2e": {"value": ws * BATCH / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "roofline": roofline,
+        "clocks": clk.summary(),
+        "gpu_launches": None,
+        "solve": {"iters_mean": statistics.mean(i["iters"] for i in step_infos), "max_resid_Lrho": resid,
+                  "nnz": nnz, "nnz_factors": nnzf, "levels": [step_infos[0]["levels_lower"],
+                                                                step_infos[0]["levels_upper"]],
+                  "ms_setup_mean": statistics.mean(i["ms_setup"] for i in step_infos),
+                  "ms_solve_mean": statistics.mean(i["ms_solve"] for i in step_infos)},
+    }
+    out["gpu_launches_profiled_per_step"] = launches_per_step
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+# ----------------------------------------------------------- CPU (oracle) arm
+
+def _oracle_solves(count: int, start_seed: int = 0):
+    from oracle.steady import steady_state_dense
+    from workloads import jaynes_cummings_rwa
+    t0 = time.perf_counter()
+    for s in range(count):
+        sysm = jaynes_cummings_rwa(seed=start_seed + s, N=JC_N)
+        steady_state_dense(sysm.H, sysm.c_ops)
+    return time.perf_counter() - t0
+
+
+def _threads():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return max(i.get("num_threads", 1) for i in info)
+    except ImportError:
+        pass
+    return len(os.sched_getaffinity(0))
+
+
+def cpu_baseline(sample: int):
+    dt = _oracle_solves(sample)
+    return {"value": sample / dt, "unit": UNIT, "cores": _threads(), "kind": "oracle",
+            "sample": f"{sample} JC40 systems (seeds 0..{sample - 1}) by the oracle's dense FP64 LU of the "
+                      f"trace-row system, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return None
+    per_step = max(1, args.cpu_sample // 2)
+    for _ in range(args.warmup and 1):
+        _oracle_solves(1, 1000)
+    times = []
+    for k in range(args.steps):
+        times.append(_oracle_solves(per_step, k * per_step))
+    ms = 1000.0 * sum(times) / len(times)
+    value = per_step / (ms / 1000.0)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "jc40: driven dissipative Jaynes-Cummings, cavity 40 x atom, n=6400",
+                       "method": "oracle dense LU", "per_step_sample": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": _threads(), "kind": "oracle",
+                             "sample": f"{per_step} JC40 systems per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--method", default="iterative-bicgstab")
+    ap.add_argument("--precond", default="ilut", choices=["ilu0", "ilut"])
+    ap.add_argument("--cpu-sample", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * lindblad_ss.h -- C ABI of the GB300 steady-state solver for open quantum
+ * systems (Nation, "Steady-state solution methods for open quantum optical
+ * systems", arXiv:1504.06768).
+ *
+ * Problem (section "Steady-state density matrix", Eq. ss / Eq. eigval):
+ * given a time-independent Hamiltonian H and collapse operators C_k, all
+ * d x d sparse complex matrices, find rho_ss with L rho_ss = 0 and
+ * Tr rho_ss = 1, where L is the Lindblad superoperator of Eq. (lindblad)
+ * acting on the column-stacked vector vec(rho) (vec(rho)[i + d*j] = rho[i,j]).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex numbers are interleaved doubles (re, im): a complex array of
+ *   length m is a double array of length 2m.  FP32 variants use floats.
+ * - Sparse matrices are CSR with int32 row pointers and column indices,
+ *   columns sorted ascending and unique within a row.  nnz < 2^31.
+ * - Views (ss_csr_view) are borrowed: the library copies what it needs and
+ *   never keeps the caller's pointers after the call returns.
+ * - Handles (ss_ctx, ss_mat, ss_prec) are owned by the library; free them
+ *   with the matching *_free / *_destroy.  Matrices and factors live in the
+ *   device memory of the context's GPU.
+ * - Vector arguments documented as "device" must be device pointers on the
+ *   context's GPU; "host" arguments are ordinary host memory.
+ * - Work is issued on the context's CUDA stream.  A call returns after the
+ *   work it started has completed, unless documented otherwise.
+ * - Every function returns an ss_status and never aborts; on failure the
+ *   reason is available from ss_last_error(ctx).  Output handles are set to
+ *   NULL on failure.
+ * - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef LINDBLAD_SS_H
+#define LINDBLAD_SS_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SS_OK = 0,
+    SS_ERR_INVALID = 1,      /* bad argument (shape, pointer, option)              */
+    SS_ERR_OOM = 2,          /* device allocation failed                           */
+    SS_NOT_CONVERGED = 3,    /* iteration cap reached; outputs hold the last iterate */
+    SS_BREAKDOWN = 4,        /* BiCGSTAB inner product vanished (section "Iterative
+                                solvers": the residual became orthogonal to the
+                                shadow residual)                                   */
+    SS_ZERO_PIVOT = 5,       /* incomplete factorisation met a zero/missing pivot  */
+    SS_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up                 */
+    SS_ERR_CUDA = 7,         /* a CUDA runtime call failed                          */
+    SS_ERR_UNSUPPORTED = 8   /* valid request this build does not implement        */
+} ss_status;
+
+typedef enum {
+    SS_METHOD_DIRECT = 0,          /* direct LU of Eq. (linear): not built (returns UNSUPPORTED) */
+    SS_METHOD_ITER_GMRES = 1,      /* "iterative-lgmres": restarted GMRES(m) on Eq. (linear) */
+    SS_METHOD_ITER_BICGSTAB = 2,   /* "iterative-bicgstab": BiCGSTAB on Eq. (linear)         */
+    SS_METHOD_INVERSE_POWER = 3    /* doubly-iterative inverse power on L - sigma I          */
+} ss_method;
+
+typedef enum { SS_PRECOND_ILU0 = 0, SS_PRECOND_ILUT = 1 } ss_precond_kind;
+
+typedef enum {
+    SS_PREC_FP64 = 0,    /* everything in complex FP64                                    */
+    SS_PREC_MIXED = 1    /* FP32 inner Krylov solve + FP32 factors, FP64 refinement       */
+} ss_precision;
+
+typedef enum { SS_KRYLOV_BICGSTAB = 0, SS_KRYLOV_GMRES = 1 } ss_krylov;
+
+/* Borrowed CSR view of a square or rectangular complex matrix. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    const int32_t* row_ptr;   /* n_rows + 1 entries                                */
+    const int32_t* col;       /* nnz entries                                        */
+    const double* val;        /* 2 * nnz doubles, interleaved (re, im)              */
+    int on_device;            /* 0: the three arrays are host memory; 1: device     */
+} ss_csr_view;
+
+typedef struct ss_ctx_s* ss_ctx;
+typedef struct ss_mat_s* ss_mat;
+typedef struct ss_prec_s* ss_prec;
+
+/* Options of steady_state().  ss_options_default() fills the defaults shown. */
+typedef struct {
+    int method;            /* ss_method; default SS_METHOD_ITER_BICGSTAB                     */
+    int precond;           /* ss_precond_kind; default SS_PRECOND_ILU0                       */
+    int precision;         /* ss_precision; default SS_PREC_FP64                             */
+    double tol;            /* accept when ||L rho||_2 <= tol, rho trace-normalised; 1e-10    */
+    int maxiter;           /* Krylov iteration cap (section "Numerical Simulations"); 1000    */
+    int restart;           /* GMRES restart length m; 30 (maximum 64)                         */
+    double drop_tol;       /* ILUT drop tolerance d (relative to the row infinity norm); 1e-4 */
+    double fill_factor;    /* ILUT fill factor p; 10                                         */
+    double w;              /* weight of Eq. (linear); <= 0 selects mean_i |L_ii|              */
+    double sigma;          /* shift of Eq. (inverse); 1e-15                                  */
+    int use_rcm;           /* reverse Cuthill-McKee ordering of L~ + L~^T; 1                 */
+    uint64_t seed;         /* inverse-power start vector (SplitMix64 counters); 0             */
+} ss_options;
+
+/* Per-solve diagnostics. */
+typedef struct {
+    int status;            /* ss_status of the solve                                   */
+    int iters;             /* Krylov iterations (inner iterations for MIXED)           */
+    int outer_iters;       /* inverse-power or refinement steps                        */
+    double resid_Lrho;     /* FP64 ||L rho||_2 of the returned trace-normalised rho     */
+    double w_used;         /* weight of Eq. (linear) (0 for inverse power)             */
+    double condest;        /* ||M^{-1} e||_inf of the preconditioner                   */
+    int64_t n, nnz;        /* size of L~ (or L - sigma I)                              */
+    int64_t bandwidth, profile;  /* of the matrix after ordering                       */
+    int64_t nnz_factors;   /* stored entries of the incomplete factors                 */
+    int32_t levels_lower, levels_upper;  /* triangular-solve level counts               */
+    double ms_setup, ms_solve;           /* wall time of setup and of the iteration      */
+} ss_info;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The stream is
+ * borrowed and must outlive the context. */
+ss_status ss_ctx_create(int device, void* cuda_stream, ss_ctx* out);
+ss_status ss_ctx_destroy(ss_ctx ctx);
+/* Replace the stream used by later calls. */
+ss_status ss_ctx_set_stream(ss_ctx ctx, void* cuda_stream);
+/* Message describing the last failure on this context ("" if none). */
+const char* ss_last_error(ss_ctx ctx);
+void ss_options_default(ss_options* opt);
+
+/* ----------------------------------------------------------- matrices */
+
+/* Assemble L (Eq. lindblad vectorised as in Eq. eigval):
+ *   L = -i (I kron H - H^T kron I)
+ *       + sum_k (conj(C_k) kron C_k - 1/2 I kron C_k^+C_k - 1/2 (C_k^+C_k)^T kron I)
+ * H and the n_c operators in c_ops are d x d views (host or device).  The
+ * result is an n x n matrix, n = d^2, built on the device from the Kronecker
+ * structure; entries whose summed value is exactly zero are not stored.
+ * Errors: SS_ERR_INVALID for non-square or mismatched views. */
+ss_status assemble_liouvillian(ss_ctx ctx, const ss_csr_view* H, int n_c, const ss_csr_view* c_ops,
+                               ss_mat* L_out);
+
+/* Eq. (linear): L~ = L + w T, T = ones in row 0 at the columns i(d+1) of the
+ * diagonal elements of rho; d = sqrt(n).  w <= 0 selects w = mean_i |L_ii|
+ * (the weight of the numerical section); the value used is written to
+ * *w_used (may be NULL).  The right-hand side of Eq. (linear) is w e_0. */
+ss_status add_trace_row(ss_ctx ctx, ss_mat L, double w, ss_mat* out, double* w_used);
+
+/* Eq. (inverse): L - sigma I.  Every diagonal entry is stored afterwards. */
+ss_status add_shift(ss_ctx ctx, ss_mat L, double sigma, ss_mat* out);
+
+/* Reverse Cuthill-McKee ordering of the pattern of A + A^T (section "Direct
+ * factorization"): breadth-first search from a node of minimum degree,
+ * neighbours by increasing degree, per connected component, reversed.
+ * Ties: the start node is the highest-index unvisited node of minimum
+ * degree; neighbours are taken in ascending (degree, index); the degree
+ * counts the stored diagonal.  perm_out (host, n int32) receives perm with
+ * perm[new] = old.  bw_out / profile_out (may be NULL) receive the
+ * bandwidth B and profile P of P A P^T. */
+ss_status rcm_permute(ss_ctx ctx, ss_mat A, int32_t* perm_out, int64_t* bw_out, int64_t* profile_out);
+
+/* out = P A P^T, out[r][c] = A[perm[r]][perm[c]]; perm is host memory, n int32. */
+ss_status permute(ss_ctx ctx, ss_mat A, const int32_t* perm, ss_mat* out);
+
+/* Bandwidth B = ub + lb + 1 and profile P = up + lp of A's stored pattern
+ * (section "Direct factorization"). */
+ss_status bandwidth_profile(ss_ctx ctx, ss_mat A, int64_t* bw_out, int64_t* profile_out);
+
+/* Size of a matrix handle. */
+ss_status ss_mat_shape(ss_mat A, int64_t* n_rows, int64_t* nnz);
+/* Copy a matrix to caller buffers (host): row_ptr n+1, col nnz, val 2 nnz. */
+ss_status ss_mat_export(ss_ctx ctx, ss_mat A, int32_t* row_ptr, int32_t* col, double* val);
+/* Wrap a CSR view as a library matrix (copied to the device). */
+ss_status ss_mat_import(ss_ctx ctx, const ss_csr_view* A, ss_mat* out);
+void ss_mat_free(ss_mat A);
+
+/* y = A x (complex FP64 CSR SpMV); x, y are device arrays of 2n doubles. */
+ss_status spmv(ss_ctx ctx, ss_mat A, const double* x, double* y);
+/* FP32 variant on A's FP32 copy (made on first use); x, y device, 2n floats. */
+ss_status spmv_f32(ss_ctx ctx, ss_mat A, const float* x, float* y);
+
+/* ------------------------------------------------------ preconditioner */
+
+/* Incomplete LU of A (section "Iterative solvers"):
+ *   kind SS_PRECOND_ILU0: no fill, computed on the device level by level;
+ *   kind SS_PRECOND_ILUT: dual threshold -- entries of row i below
+ *     drop_tol * ||a_i||_inf are dropped and each of the strict L and U parts
+ *     keeps at most ceil(fill_factor * nnz(a_i) / 2) largest entries; no
+ *     pivoting; computed on the host.
+ * precision: SS_PREC_FP64, or SS_PREC_MIXED to also keep FP32 factors.
+ * condest_out (may be NULL): ||M^{-1} e||_inf, e = ones.
+ * Errors: SS_ZERO_PIVOT when a pivot is missing or zero. */
+ss_status ilu_factor(ss_ctx ctx, ss_mat A, int kind, double drop_tol, double fill_factor,
+                     int precision, ss_prec* out, double* condest_out);
+/* z = U^{-1} L^{-1} r (level-scheduled sparse triangular solves); device, 2n doubles. */
+ss_status precond_apply(ss_ctx ctx, ss_prec M, const double* r, double* z);
+/* FP32 variant (needs precision SS_PREC_MIXED at factorisation). */
+ss_status precond_apply_f32(ss_ctx ctx, ss_prec M, const float* r, float* z);
+/* Factor sizes and level counts. */
+ss_status ss_prec_info(ss_prec M, int64_t* nnz, int32_t* levels_lower, int32_t* levels_upper);
+/* Copy the combined factors (strict lower = L with unit diagonal, rest = U)
+ * into host buffers: row_ptr n+1, col nnz, val 2 nnz. */
+ss_status ss_prec_export(ss_ctx ctx, ss_prec M, int32_t* row_ptr, int32_t* col, double* val);
+void ss_prec_free(ss_prec M);
+
+/* ------------------------------------------------------------ solvers */
+
+/* Solve A x = b with right-preconditioned BiCGSTAB or GMRES(restart)
+ * (section "Iterative solvers"), M from ilu_factor on the same A.  b and x
+ * are device arrays (2n doubles); x holds the initial guess on entry.
+ * Stops when the updated residual satisfies ||b - A x||_2 <= tol (absolute)
+ * or after maxiter iterations (SS_NOT_CONVERGED); SS_BREAKDOWN when a
+ * BiCGSTAB inner product vanishes.  *iters_out (may be NULL) receives the
+ * iteration count, *resid_out (may be NULL) the final residual norm. */
+ss_status krylov_solve(ss_ctx ctx, ss_mat A, ss_prec M, int krylov, const double* b, double* x,
+                       double tol, int maxiter, int restart, int* iters_out, double* resid_out);
+
+/* Full steady-state solve.  H and c_ops as for assemble_liouvillian.
+ * rho_out: d*d complex (2 d^2 doubles), column-major, trace-normalised;
+ * host memory if rho_on_device == 0, device memory otherwise.  info may be
+ * NULL.  Returns SS_OK when ||L rho||_2 <= opt->tol; SS_NOT_CONVERGED or
+ * SS_BREAKDOWN still write the last iterate to rho_out. */
+ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, const ss_csr_view* c_ops,
+                       const ss_options* opt, double* rho_out, int rho_on_device, ss_info* info);
+
+/* ---------------------------------------------------------- diagnostics */
+
+/* Kernel classes of the per-launch profiler. */
+typedef enum { SS_PROF_SPMV = 0, SS_PROF_TRSV_LOWER = 1, SS_PROF_TRSV_UPPER = 2 } ss_prof_kind;
+
+/* When enabled, CUDA events are recorded on the context's stream around every
+ * SpMV and triangular-solve launch issued through this context.  Not part of
+ * the paper: a measurement aid for the bandwidth roofline. */
+ss_status ss_profile_enable(ss_ctx ctx, int enable);
+/* Synchronise the stream and return, for one kernel class, the number of
+ * launches recorded since the last read and their summed device time in
+ * milliseconds; the records of that class are then cleared. */
+ss_status ss_profile_read(ss_ctx ctx, int kind, int64_t* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LINDBLAD_SS_H */

@@ -1,0 +1,322 @@
+"""GB300 steady-state solver for open quantum systems (arXiv:1504.06768).
+
+A thin Python layer over the C ABI of liblindblad_ss.so (include/lindblad_ss.h):
+it converts SciPy sparse operators to CSR views and torch CUDA tensors to
+device pointers, and nothing else.  The functions keep the C names:
+
+    assemble_liouvillian, add_trace_row, add_shift, rcm_permute, permute,
+    bandwidth_profile, ilu_factor, spmv, precond_apply, krylov_solve,
+    steady_state
+
+Device memory and streams come from PyTorch; all arithmetic runs in the CUDA
+library.  Importing works without a GPU; calls need one.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import _binding as B
+
+__all__ = ["SolverError", "Context", "Matrix", "Preconditioner", "get_context", "assemble_liouvillian",
+           "add_trace_row", "add_shift", "rcm_permute", "permute", "bandwidth_profile", "ilu_factor",
+           "spmv", "spmv_f32", "precond_apply", "precond_apply_f32", "krylov_solve", "steady_state",
+           "library_path"]
+
+
+def library_path() -> str:
+    return B.LIB_PATH
+
+
+class SolverError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{B.STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class Context:
+    """Owns an ss_ctx bound to one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        lib = B.load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.device = device
+        self.stream = stream
+        h = C.c_void_p()
+        st = lib.ss_ctx_create(device, C.c_void_p(stream.cuda_stream), C.byref(h))
+        if st != 0:
+            raise SolverError(st, "ss_ctx_create failed")
+        self.handle = h
+
+    def check(self, st: int, what: str):
+        if st != 0:
+            msg = B.load().ss_last_error(self.handle).decode()
+            raise SolverError(st, f"{what}: {msg}")
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and B._lib is not None:
+            B._lib.ss_ctx_destroy(h)
+            self.handle = None
+
+
+_contexts: dict = {}
+
+
+def get_context(device: int = 0) -> Context:
+    ctx = _contexts.get(device)
+    if ctx is None:
+        ctx = Context(device)
+        _contexts[device] = ctx
+    return ctx
+
+
+class _CsrHost:
+    """Keeps the numpy arrays of a CSR view alive for the duration of a call."""
+
+    def __init__(self, m):
+        import scipy.sparse as sp
+        m = sp.csr_matrix(m, dtype=np.complex128)
+        m.sum_duplicates()
+        m.sort_indices()
+        self.rp = np.ascontiguousarray(m.indptr, dtype=np.int32)
+        self.col = np.ascontiguousarray(m.indices, dtype=np.int32)
+        self.val = np.ascontiguousarray(m.data, dtype=np.complex128)
+        self.view = B.CsrView(m.shape[0], m.shape[1], m.nnz, self.rp.ctypes.data, self.col.ctypes.data,
+                              self.val.ctypes.data, 0)
+
+
+class Matrix:
+    """A library-owned complex FP64 CSR matrix on the device."""
+
+    def __init__(self, ctx: Context, handle: C.c_void_p):
+        self.ctx = ctx
+        self.handle = handle
+
+    @property
+    def shape(self):
+        n, nnz = C.c_int64(), C.c_int64()
+        B.load().ss_mat_shape(self.handle, C.byref(n), C.byref(nnz))
+        return (n.value, n.value)
+
+    @property
+    def nnz(self) -> int:
+        n, nnz = C.c_int64(), C.c_int64()
+        B.load().ss_mat_shape(self.handle, C.byref(n), C.byref(nnz))
+        return nnz.value
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+        n, nnz = self.shape[0], self.nnz
+        rp = np.empty(n + 1, dtype=np.int32)
+        col = np.empty(max(nnz, 1), dtype=np.int32)
+        val = np.empty(max(nnz, 1), dtype=np.complex128)
+        self.ctx.check(B.load().ss_mat_export(self.ctx.handle, self.handle, rp.ctypes.data, col.ctypes.data,
+                                              val.ctypes.data), "ss_mat_export")
+        return sp.csr_matrix((val[:nnz], col[:nnz], rp), shape=(n, n))
+
+    @classmethod
+    def from_scipy(cls, m, ctx: Optional[Context] = None) -> "Matrix":
+        ctx = ctx or get_context()
+        hv = _CsrHost(m)
+        h = C.c_void_p()
+        ctx.check(B.load().ss_mat_import(ctx.handle, C.byref(hv.view), C.byref(h)), "ss_mat_import")
+        return cls(ctx, h)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and B._lib is not None:
+            B._lib.ss_mat_free(h)
+            self.handle = None
+
+
+class Preconditioner:
+    def __init__(self, ctx: Context, handle: C.c_void_p, condest: float):
+        self.ctx = ctx
+        self.handle = handle
+        self.condest = condest
+
+    def info(self) -> dict:
+        nnz, lo, up = C.c_int64(), C.c_int32(), C.c_int32()
+        B.load().ss_prec_info(self.handle, C.byref(nnz), C.byref(lo), C.byref(up))
+        return {"nnz": nnz.value, "levels_lower": lo.value, "levels_upper": up.value}
+
+    def to_scipy(self, n: int):
+        import scipy.sparse as sp
+        nnz = self.info()["nnz"]
+        rp = np.empty(n + 1, dtype=np.int32)
+        col = np.empty(max(nnz, 1), dtype=np.int32)
+        val = np.empty(max(nnz, 1), dtype=np.complex128)
+        self.ctx.check(B.load().ss_prec_export(self.ctx.handle, self.handle, rp.ctypes.data, col.ctypes.data,
+                                               val.ctypes.data), "ss_prec_export")
+        return sp.csr_matrix((val[:nnz], col[:nnz], rp), shape=(n, n))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and B._lib is not None:
+            B._lib.ss_prec_free(h)
+            self.handle = None
+
+
+def _dev_ptr(t, dtype_name: str, n: int):
+    import torch
+    want = {"c128": torch.complex128, "c64": torch.complex64}[dtype_name]
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == want and t.is_contiguous()
+            and t.numel() == n):
+        raise ValueError(f"expected a contiguous CUDA {want} tensor of {n} elements")
+    return C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------- API
+
+def assemble_liouvillian(H, c_ops: Sequence, ctx: Optional[Context] = None) -> Matrix:
+    """L of Eq. (lindblad), column-stacked (Eq. eigval), assembled on the GPU."""
+    ctx = ctx or get_context()
+    hv = _CsrHost(H)
+    cvs = [_CsrHost(c) for c in c_ops]
+    arr = (B.CsrView * max(len(cvs), 1))(*[c.view for c in cvs])
+    h = C.c_void_p()
+    ctx.check(B.load().assemble_liouvillian(ctx.handle, C.byref(hv.view), len(cvs), arr, C.byref(h)),
+              "assemble_liouvillian")
+    return Matrix(ctx, h)
+
+
+def add_trace_row(L: Matrix, w: float = 0.0):
+    """Eq. (linear): returns (L + w T, w_used); w <= 0 selects mean |L_ii|."""
+    h, wu = C.c_void_p(), C.c_double()
+    L.ctx.check(B.load().add_trace_row(L.ctx.handle, L.handle, w, C.byref(h), C.byref(wu)), "add_trace_row")
+    return Matrix(L.ctx, h), wu.value
+
+
+def add_shift(L: Matrix, sigma: float = 1e-15) -> Matrix:
+    """Eq. (inverse): L - sigma I."""
+    h = C.c_void_p()
+    L.ctx.check(B.load().add_shift(L.ctx.handle, L.handle, sigma, C.byref(h)), "add_shift")
+    return Matrix(L.ctx, h)
+
+
+def rcm_permute(A: Matrix):
+    """Reverse Cuthill-McKee of A + A^T: (perm with perm[new] = old, B, P)."""
+    n = A.shape[0]
+    perm = np.empty(n, dtype=np.int32)
+    bw, prof = C.c_int64(), C.c_int64()
+    A.ctx.check(B.load().rcm_permute(A.ctx.handle, A.handle, perm.ctypes.data, C.byref(bw), C.byref(prof)),
+                "rcm_permute")
+    return perm, bw.value, prof.value
+
+
+def permute(A: Matrix, perm) -> Matrix:
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    h = C.c_void_p()
+    A.ctx.check(B.load().permute(A.ctx.handle, A.handle, perm.ctypes.data, C.byref(h)), "permute")
+    return Matrix(A.ctx, h)
+
+
+def bandwidth_profile(A: Matrix):
+    bw, prof = C.c_int64(), C.c_int64()
+    A.ctx.check(B.load().bandwidth_profile(A.ctx.handle, A.handle, C.byref(bw), C.byref(prof)),
+                "bandwidth_profile")
+    return bw.value, prof.value
+
+
+def ilu_factor(A: Matrix, kind: str = "ilu0", drop_tol: float = 1e-4, fill_factor: float = 10.0,
+               precision: str = "fp64") -> Preconditioner:
+    h, ce = C.c_void_p(), C.c_double()
+    A.ctx.check(B.load().ilu_factor(A.ctx.handle, A.handle, B.PRECONDS[kind], drop_tol, fill_factor,
+                                    B.PRECISIONS[precision], C.byref(h), C.byref(ce)), "ilu_factor")
+    return Preconditioner(A.ctx, h, ce.value)
+
+
+def spmv(A: Matrix, x):
+    import torch
+    n = A.shape[0]
+    y = torch.empty(n, dtype=torch.complex128, device=x.device)
+    A.ctx.check(B.load().spmv(A.ctx.handle, A.handle, _dev_ptr(x, "c128", n), _dev_ptr(y, "c128", n)), "spmv")
+    return y
+
+
+def spmv_f32(A: Matrix, x):
+    import torch
+    n = A.shape[0]
+    y = torch.empty(n, dtype=torch.complex64, device=x.device)
+    A.ctx.check(B.load().spmv_f32(A.ctx.handle, A.handle, _dev_ptr(x, "c64", n), _dev_ptr(y, "c64", n)),
+                "spmv_f32")
+    return y
+
+
+def precond_apply(M: Preconditioner, r):
+    import torch
+    n = r.numel()
+    z = torch.empty_like(r)
+    M.ctx.check(B.load().precond_apply(M.ctx.handle, M.handle, _dev_ptr(r, "c128", n), _dev_ptr(z, "c128", n)),
+                "precond_apply")
+    return z
+
+
+def precond_apply_f32(M: Preconditioner, r):
+    import torch
+    n = r.numel()
+    z = torch.empty_like(r)
+    M.ctx.check(B.load().precond_apply_f32(M.ctx.handle, M.handle, _dev_ptr(r, "c64", n),
+                                           _dev_ptr(z, "c64", n)), "precond_apply_f32")
+    return z
+
+
+def krylov_solve(A: Matrix, M: Preconditioner, b, x0=None, method: str = "bicgstab", tol: float = 1e-12,
+                 maxiter: int = 1000, restart: int = 30, raise_on_failure: bool = False):
+    """Right-preconditioned BiCGSTAB / GMRES(m) on A x = b; returns (x, status, iters, resid)."""
+    import torch
+    n = A.shape[0]
+    x = torch.zeros_like(b) if x0 is None else x0.clone()
+    it, res = C.c_int(), C.c_double()
+    st = B.load().krylov_solve(A.ctx.handle, A.handle, M.handle, B.KRYLOV[method], _dev_ptr(b, "c128", n),
+                               _dev_ptr(x, "c128", n), tol, maxiter, restart, C.byref(it), C.byref(res))
+    if st not in (B.SS_OK, B.SS_NOT_CONVERGED, B.SS_BREAKDOWN) or (raise_on_failure and st != 0):
+        A.ctx.check(st, "krylov_solve")
+    return x, st, it.value, res.value
+
+
+def steady_state(H, c_ops: Sequence, method: str = "iterative-bicgstab", tol: float = 1e-10,
+                 precond: str = "ilu0", precision: str = "fp64", maxiter: int = 1000, restart: int = 30,
+                 drop_tol: float = 1e-4, fill_factor: float = 10.0, w: float = 0.0, sigma: float = 1e-15,
+                 use_rcm: bool = True, seed: int = 0, ctx: Optional[Context] = None, out=None,
+                 raise_on_failure: bool = True):
+    """rho_ss (d x d complex128, trace one) and the solve's info dict.
+
+    out: optional CUDA complex128 tensor of d*d elements (column-major rho);
+    when given, rho is written there and returned as a (d, d) view (transposed
+    storage); otherwise a numpy array is returned.
+    """
+    ctx = ctx or get_context()
+    hv = _CsrHost(H)
+    cvs = [_CsrHost(c) for c in c_ops]
+    arr = (B.CsrView * max(len(cvs), 1))(*[c.view for c in cvs])
+    opt = B.Options()
+    B.load().ss_options_default(C.byref(opt))
+    opt.method = B.METHODS[method]
+    opt.precond = B.PRECONDS[precond]
+    opt.precision = B.PRECISIONS[precision]
+    opt.tol, opt.maxiter, opt.restart = tol, maxiter, restart
+    opt.drop_tol, opt.fill_factor, opt.w, opt.sigma = drop_tol, fill_factor, w, sigma
+    opt.use_rcm, opt.seed = int(bool(use_rcm)), seed
+    d = hv.view.n_rows
+    info = B.Info()
+    if out is None:
+        rho = np.empty(d * d, dtype=np.complex128)
+        ptr, on_dev = rho.ctypes.data, 0
+    else:
+        ptr, on_dev = _dev_ptr(out, "c128", d * d), 1
+    st = B.load().steady_state(ctx.handle, C.byref(hv.view), len(cvs), arr, C.byref(opt), ptr, on_dev,
+                               C.byref(info))
+    if st != 0 and (raise_on_failure or st not in (B.SS_NOT_CONVERGED, B.SS_BREAKDOWN)):
+        ctx.check(st, "steady_state")
+    result = rho.reshape((d, d), order="F") if out is None else out.view(d, d).T
+    return result, info.as_dict()

@@ -1,0 +1,174 @@
+// Internal declarations shared by the solver's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lindblad_ss.h"
+
+// ------------------------------------------------------------ complex math
+// Complex FP64 / FP32 numbers are double2 / float2 (x = re, y = im).
+
+__host__ __device__ __forceinline__ double2 cmake(double re, double im) { return make_double2(re, im); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// Smith's algorithm (R. L. Smith, "Algorithm 116: Complex division", CACM 1962).
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, den = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / den, (a.y - a.x * r) / den);
+    } else {
+        double r = b.x / b.y, den = b.y + b.x * r;
+        return make_double2((a.x * r + a.y) / den, (a.y * r - a.x) / den);
+    }
+}
+
+__host__ __device__ __forceinline__ float2 fcadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 fcsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 fcmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// ---------------------------------------------------------------- handles
+
+struct DeviceCSR {          // complex FP64 CSR on the device
+    int64_t n_rows = 0, n_cols = 0, nnz = 0;
+    int32_t* row_ptr = nullptr;
+    int32_t* col = nullptr;
+    double2* val = nullptr;
+};
+
+// Kernel classes timed by the optional per-launch profiler.
+enum ProfKind { PROF_SPMV = 0, PROF_TRSV_LOWER = 1, PROF_TRSV_UPPER = 2, PROF_NKINDS = 3 };
+
+struct ProfRec {
+    cudaEvent_t a, b;
+    int kind;
+};
+
+struct ss_ctx_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    int num_sms = 0;
+    int prof = 0;                       // record events around SpMV / triangular-solve launches
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+    // persistent scratch (grown on demand)
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    double* h_pinned = nullptr;      // small pinned host buffer for scalars
+};
+
+struct ss_mat_s {
+    DeviceCSR m;
+    int32_t* diag_pos = nullptr;      // position of the diagonal entry per row (-1 if absent)
+    float2* val32 = nullptr;          // FP32 copy of the values (made on demand)
+    int64_t d = 0;                    // Hilbert dimension when the matrix is a Liouvillian (n = d^2)
+};
+
+struct TriLevels {                    // level-scheduled triangular factor
+    int32_t n_levels = 0;
+    int32_t* order = nullptr;         // rows sorted by level (device, n)
+    int32_t* units = nullptr;         // level-aligned units of 32/g rows, -1 padded (device)
+    int64_t n_units = 0;
+    int g = 32;                       // lanes per row in the solve
+};
+
+struct ss_prec_s {
+    DeviceCSR f;                      // combined factors: strict lower = L (unit), rest = U
+    int32_t* diag_pos = nullptr;      // device, n
+    double2* inv_diag = nullptr;      // 1 / u_ii (device, n)
+    float2* val32 = nullptr;          // FP32 factors (mixed precision)
+    float2* inv_diag32 = nullptr;
+    TriLevels lower, upper;
+    uint32_t* flags = nullptr;        // per-row completion flags for the sync-free solves
+    unsigned long long* tickets = nullptr;  // [0] lower, [1] upper
+    int* err = nullptr;               // device error word (bounded waits)
+    double2* tmp = nullptr;           // intermediate vector of the two solves
+    float2* tmp32 = nullptr;
+};
+
+// ----------------------------------------------------------------- errors
+
+ss_status set_error(ss_ctx ctx, ss_status st, const std::string& msg);
+ss_status cuda_check(ss_ctx ctx, cudaError_t e, const char* what);
+
+#define SS_CUDA(ctx, call)                                              \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return cuda_check((ctx), _e, #call);     \
+    } while (0)
+
+#define SS_TRY(call)                                                    \
+    do {                                                                \
+        ss_status _s = (call);                                          \
+        if (_s != SS_OK) return _s;                                     \
+    } while (0)
+
+// RAII event pair around one launch when the context's profiler is on.
+struct ProfScope {
+    ss_ctx c;
+    int kind;
+    cudaEvent_t a = nullptr;
+    ProfScope(ss_ctx ctx, int k);
+    ~ProfScope();
+};
+
+// ------------------------------------------------------------ allocation
+
+ss_status dev_alloc(ss_ctx ctx, void** p, size_t bytes);
+void dev_free(ss_ctx ctx, void* p);
+void dev_free_nostream(void* p);
+template <class T> ss_status dev_alloc_n(ss_ctx ctx, T** p, size_t n) {
+    return dev_alloc(ctx, reinterpret_cast<void**>(p), n * sizeof(T) + (n == 0 ? 16 : 0));
+}
+void free_csr(ss_ctx ctx, DeviceCSR& m);
+
+// --------------------------------------------------------- device helpers
+
+// Exclusive scan of n int32 counts into n+1 offsets (out[0] = 0, out[n] = total);
+// returns the total in *total (host) and fails with SS_ERR_UNSUPPORTED past 2^31-1.
+ss_status exclusive_scan_i32(ss_ctx ctx, const int32_t* counts, int32_t* out, int64_t n, int64_t* total);
+// Position of the diagonal entry in each row (-1 when absent).
+ss_status find_diag(ss_ctx ctx, const DeviceCSR& m, int32_t* diag_pos);
+ss_status upload_csr(ss_ctx ctx, const ss_csr_view* v, DeviceCSR& out);
+
+// ----------------------------------------------------------- kernels API
+
+ss_status assemble_impl(ss_ctx ctx, const DeviceCSR& H, const std::vector<DeviceCSR>& C, DeviceCSR& L);
+ss_status add_trace_row_impl(ss_ctx ctx, const DeviceCSR& L, int64_t d, double w, DeviceCSR& out);
+ss_status mean_abs_diag(ss_ctx ctx, const DeviceCSR& L, double* w);
+ss_status add_shift_impl(ss_ctx ctx, const DeviceCSR& L, double sigma, DeviceCSR& out);
+ss_status permute_impl(ss_ctx ctx, const DeviceCSR& A, const int32_t* perm_host, DeviceCSR& out);
+ss_status bandwidth_profile_impl(ss_ctx ctx, const DeviceCSR& A, int64_t* bw, int64_t* prof);
+
+#include "host_algos.h"
+
+// preconditioner
+ss_status ilu0_device(ss_ctx ctx, const DeviceCSR& A, ss_prec M);
+ss_status prec_finish(ss_ctx ctx, ss_prec M, bool want_fp32);
+ss_status prec_apply_dev(ss_ctx ctx, ss_prec M, const double2* r, double2* z, const int* halt = nullptr);
+ss_status prec_apply_dev32(ss_ctx ctx, ss_prec M, const float2* r, float2* z, const int* halt = nullptr);
+ss_status prec_from_host(ss_ctx ctx, ss_prec M, int64_t n, const std::vector<int32_t>& rp,
+                         const std::vector<int32_t>& col, const std::vector<double>& val);
+ss_status prec_check_error(ss_ctx ctx, ss_prec M);
+void prec_destroy(ss_ctx ctx, ss_prec M);
+
+// SpMV
+ss_status spmv_dev(ss_ctx ctx, const DeviceCSR& A, const double2* x, double2* y);
+ss_status spmv_dev32(ss_ctx ctx, const DeviceCSR& A, const float2* val32, const float2* x, float2* y);

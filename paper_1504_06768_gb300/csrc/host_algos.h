@@ -1,0 +1,35 @@
+// Host-side (C++) algorithms of the solver: ordering, level analysis, ILUT.
+// Plain C++17, no CUDA types, so these translation units build with g++.
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+// Reverse Cuthill-McKee order of the pattern of A + A^T (A: n x n CSR).
+// perm[new] = old.  Start node: highest-index unvisited node of minimum
+// degree; neighbours in ascending (degree, index); degree counts the stored
+// diagonal.
+void rcm_host(int64_t n, const int32_t* row_ptr, const int32_t* col, int32_t* perm);
+
+// Level sets of the strict lower (lower = true) or strict upper triangle of
+// a CSR pattern: level(i) = 1 + max level of the rows i depends on.  Fills
+// `order` with the rows sorted by (level, row) -- for the upper triangle the
+// rows are visited from the last to the first -- and returns the number of
+// levels.  level_ptr (size levels + 1) receives the start of each level in
+// `order`.
+int32_t level_sets_host(int64_t n, const int32_t* row_ptr, const int32_t* col, bool lower,
+                        std::vector<int32_t>& order, std::vector<int32_t>& level_ptr);
+
+// Level-aligned units of R rows for the triangular solves: every unit holds
+// up to R rows of one level (padded with -1), units follow level order.
+void level_units_host(const std::vector<int32_t>& order, const std::vector<int32_t>& level_ptr, int R,
+                      std::vector<int32_t>& units);
+
+// ILUT(drop_tol, fill_factor) without pivoting on an n x n CSR matrix with
+// interleaved complex values.  Output: combined factors (strict lower part =
+// L with unit diagonal, diagonal and upper part = U), sorted columns.
+// Returns 0, or 1 + the row index of a zero or missing pivot.
+int64_t ilut_host(int64_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
+                  double drop_tol, double fill_factor, std::vector<int32_t>& f_row_ptr,
+                  std::vector<int32_t>& f_col, std::vector<double>& f_val);

@@ -1,0 +1,53 @@
+// SpMV kernel template (shared by the solver drivers).
+#pragma once
+
+#include "common.cuh"
+
+template <class T> struct SpmvOps;
+template <> struct SpmvOps<double2> {
+    __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+    __device__ static double2 madd(double2 a, double2 b, double2 c) {
+        return make_double2(c.x + a.x * b.x - a.y * b.y, c.y + a.x * b.y + a.y * b.x);
+    }
+    __device__ static double2 shfl_down(double2 v, int o, unsigned mask) {
+        return make_double2(__shfl_down_sync(mask, v.x, o), __shfl_down_sync(mask, v.y, o));
+    }
+};
+template <> struct SpmvOps<float2> {
+    __device__ static float2 zero() { return make_float2(0.f, 0.f); }
+    __device__ static float2 madd(float2 a, float2 b, float2 c) {
+        return make_float2(c.x + a.x * b.x - a.y * b.y, c.y + a.x * b.y + a.y * b.x);
+    }
+    __device__ static float2 shfl_down(float2 v, int o, unsigned mask) {
+        return make_float2(__shfl_down_sync(mask, v.x, o), __shfl_down_sync(mask, v.y, o));
+    }
+};
+
+// y[i] = sum_t A[i, col[t]] x[col[t]]; G lanes per row.  `halt` (may be null)
+// lets a solver skip launches it has already queued once it has converged.
+template <int G, class V, class T>
+__global__ void __launch_bounds__(256) spmv_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                   const V* __restrict__ val, int64_t n, const T* __restrict__ x,
+                                                   T* __restrict__ y, const int* __restrict__ halt) {
+    if (halt && *halt) return;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = gid / G;
+    const int sub = threadIdx.x % G;
+    T acc = SpmvOps<T>::zero();
+    if (row < n) {
+        const int32_t a = rp[row], b = rp[row + 1];
+        for (int32_t t = a + sub; t < b; t += G) acc = SpmvOps<T>::madd(val[t], __ldg(&x[col[t]]), acc);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        T other = SpmvOps<T>::shfl_down(acc, o, 0xffffffffu);
+        acc.x += other.x;
+        acc.y += other.y;
+    }
+    if (row < n && sub == 0) y[row] = acc;
+}
+
+int spmv_group_size(int64_t n_rows, int64_t nnz);
+void spmv_launch(const DeviceCSR& A, const double2* x, double2* y, const int* halt, cudaStream_t s);
+void spmv_launch32(const DeviceCSR& A, const float2* val32, const float2* x, float2* y, const int* halt,
+                   cudaStream_t s);
