@@ -167,25 +167,31 @@ def run_gpu(args):
     lib.ss_options_default(C.byref(opt))
     opt.method = B.METHODS[args.method]
     opt.precond = B.PRECONDS[precond]
+    opt.precision = B.PRECISIONS[args.precision]
     opt.tol = TOL
-    info = B.Info()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     infos = []
 
+    def arrays(inputs, host):
+        Hs = (B.CsrView * BATCH)(*[(hv.view if host else hv) for hv, _, _ in inputs])
+        ncs = (C.c_int * BATCH)(*[nc for _, _, nc in inputs])
+        cptrs = (C.POINTER(B.CsrView) * BATCH)(*[C.cast(arr, C.POINTER(B.CsrView)) for _, arr, _ in inputs])
+        return Hs, ncs, cptrs
+
+    dev_arr = arrays(dev_inputs, False)
+    host_arr = arrays(host_arrays, True)
+    out_dev = (C.c_void_p * BATCH)(*[rho_dev[k].data_ptr() for k in range(BATCH)])
+    out_host = (C.c_void_p * BATCH)(*[rho_host[k].data_ptr() for k in range(BATCH)])
+    info_arr = (B.Info * BATCH)()
+
     def step(host=False):
-        for k in range(BATCH):
-            if host:
-                hv, arr, nc = host_arrays[k]
-                st = lib.steady_state(ctx.handle, C.byref(hv.view), nc, arr, C.byref(opt),
-                                      C.c_void_p(rho_host[k].data_ptr()), 0, C.byref(info))
-            else:
-                hv, arr, nc = dev_inputs[k]
-                st = lib.steady_state(ctx.handle, C.byref(hv), nc, arr, C.byref(opt),
-                                      C.c_void_p(rho_dev[k].data_ptr()), 1, C.byref(info))
-            if st != 0:
-                raise RuntimeError(f"steady_state failed: {B.STATUS_NAMES.get(st)} "
-                                   f"{lib.ss_last_error(ctx.handle).decode()}")
-            infos.append(info.as_dict())
+        Hs, ncs, cptrs = host_arr if host else dev_arr
+        st = lib.steady_state_batched(ctx.handle, BATCH, Hs, ncs, cptrs, C.byref(opt),
+                                      out_host if host else out_dev, 0 if host else 1, info_arr)
+        if st != 0:
+            raise RuntimeError(f"steady_state_batched failed: {B.STATUS_NAMES.get(st)} "
+                               f"{lib.ss_last_error(ctx.handle).decode()}")
+        infos.extend(info_arr[k].as_dict() for k in range(BATCH))
 
     def barrier():
         torch.cuda.synchronize()
@@ -367,7 +373,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--method", default="iterative-bicgstab")
-    ap.add_argument("--precond", default="ilut", choices=["ilu0", "ilut"])
+    ap.add_argument("--precond", default="ilu0", choices=["ilu0", "ilut"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--cpu-sample", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -221,6 +221,23 @@ ss_status krylov_solve(ss_ctx ctx, ss_mat A, ss_prec M, int krylov, const double
 ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, const ss_csr_view* c_ops,
                        const ss_options* opt, double* rho_out, int rho_on_device, ss_info* info);
 
+/* Steady states of n_sys independent systems (parameter sweeps, uneven
+ * Hilbert sizes).  System k is H[k] with the n_c[k] operators c_ops[k]; rho_out[k]
+ * receives d_k * d_k complex values (column-major), host or device memory as
+ * rho_on_device says; infos (may be NULL) receives n_sys entries.
+ * With method = iterative-bicgstab and precond = iLU(0), systems with
+ * n = d^2 up to 11,520 (FP64) or 19,200 (SS_PREC_MIXED) are solved together by
+ * one persistent kernel launch: one thread block per system at a time runs the
+ * iLU(0) factorisation, the preconditioned BiCGSTAB (FP64, or FP32 inner
+ * iterations on r/||r|| refined in FP64 until ||L rho||_2 <= tol) and the
+ * finalisation.  Systems sharing a sparsity pattern share one RCM ordering and
+ * level schedule.  Other systems and options go through steady_state() one at
+ * a time.  Returns SS_OK when every system converged, otherwise the status of
+ * a failing system (each info holds its own status). */
+ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_view* H, const int* n_c,
+                               const ss_csr_view* const* c_ops, const ss_options* opt,
+                               double* const* rho_out, int rho_on_device, ss_info* infos);
+
 /* ---------------------------------------------------------- diagnostics */
 
 /* Kernel classes of the per-launch profiler. */

@@ -23,7 +23,7 @@ from . import _binding as B
 __all__ = ["SolverError", "Context", "Matrix", "Preconditioner", "get_context", "assemble_liouvillian",
            "add_trace_row", "add_shift", "rcm_permute", "permute", "bandwidth_profile", "ilu_factor",
            "spmv", "spmv_f32", "precond_apply", "precond_apply_f32", "krylov_solve", "steady_state",
-           "library_path"]
+           "steady_state_batched", "library_path"]
 
 
 def library_path() -> str:
@@ -284,6 +284,43 @@ def krylov_solve(A: Matrix, M: Preconditioner, b, x0=None, method: str = "bicgst
     return x, st, it.value, res.value
 
 
+def _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed):
+    opt = B.Options()
+    B.load().ss_options_default(C.byref(opt))
+    opt.method = B.METHODS[method]
+    opt.precond = B.PRECONDS[precond]
+    opt.precision = B.PRECISIONS[precision]
+    opt.tol, opt.maxiter, opt.restart = tol, maxiter, restart
+    opt.drop_tol, opt.fill_factor, opt.w, opt.sigma = drop_tol, fill_factor, w, sigma
+    opt.use_rcm, opt.seed = int(bool(use_rcm)), seed
+    return opt
+
+
+def steady_state_batched(systems: Sequence, method: str = "iterative-bicgstab", tol: float = 1e-10,
+                         precond: str = "ilu0", precision: str = "fp64", maxiter: int = 1000, restart: int = 30,
+                         drop_tol: float = 1e-4, fill_factor: float = 10.0, w: float = 0.0, sigma: float = 1e-15,
+                         use_rcm: bool = True, seed: int = 0, ctx: Optional[Context] = None,
+                         raise_on_failure: bool = True):
+    """Steady states of many systems, each given as (H, c_ops); returns a list
+    of rho (numpy, d x d) and a list of info dicts."""
+    ctx = ctx or get_context()
+    hosts = [(_CsrHost(H), [_CsrHost(c) for c in cs]) for H, cs in systems]
+    ns = len(hosts)
+    Hs = (B.CsrView * max(ns, 1))(*[h.view for h, _ in hosts])
+    ncs = (C.c_int * max(ns, 1))(*[len(cs) for _, cs in hosts])
+    carrs = [(B.CsrView * max(len(cs), 1))(*[c.view for c in cs]) for _, cs in hosts]
+    cptrs = (C.POINTER(B.CsrView) * max(ns, 1))(*[C.cast(a, C.POINTER(B.CsrView)) for a in carrs])
+    rhos = [np.empty(h.view.n_rows ** 2, dtype=np.complex128) for h, _ in hosts]
+    outs = (C.c_void_p * max(ns, 1))(*[r.ctypes.data for r in rhos])
+    infos = (B.Info * max(ns, 1))()
+    opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed)
+    st = B.load().steady_state_batched(ctx.handle, ns, Hs, ncs, cptrs, C.byref(opt), outs, 0, infos)
+    if st != 0 and (raise_on_failure or st not in (B.SS_NOT_CONVERGED, B.SS_BREAKDOWN)):
+        ctx.check(st, "steady_state_batched")
+    d = [h.view.n_rows for h, _ in hosts]
+    return [r.reshape((dk, dk), order="F") for r, dk in zip(rhos, d)], [infos[k].as_dict() for k in range(ns)]
+
+
 def steady_state(H, c_ops: Sequence, method: str = "iterative-bicgstab", tol: float = 1e-10,
                  precond: str = "ilu0", precision: str = "fp64", maxiter: int = 1000, restart: int = 30,
                  drop_tol: float = 1e-4, fill_factor: float = 10.0, w: float = 0.0, sigma: float = 1e-15,
@@ -299,14 +336,7 @@ def steady_state(H, c_ops: Sequence, method: str = "iterative-bicgstab", tol: fl
     hv = _CsrHost(H)
     cvs = [_CsrHost(c) for c in c_ops]
     arr = (B.CsrView * max(len(cvs), 1))(*[c.view for c in cvs])
-    opt = B.Options()
-    B.load().ss_options_default(C.byref(opt))
-    opt.method = B.METHODS[method]
-    opt.precond = B.PRECONDS[precond]
-    opt.precision = B.PRECISIONS[precision]
-    opt.tol, opt.maxiter, opt.restart = tol, maxiter, restart
-    opt.drop_tol, opt.fill_factor, opt.w, opt.sigma = drop_tol, fill_factor, w, sigma
-    opt.use_rcm, opt.seed = int(bool(use_rcm)), seed
+    opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed)
     d = hv.view.n_rows
     info = B.Info()
     if out is None:

@@ -81,6 +81,9 @@ _SIGNATURES = {
     "ss_prec_free": (None, [_P]),
     "krylov_solve": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, C.c_double, C.c_int, C.c_int,
                                C.POINTER(C.c_int), _DP]),
+    "steady_state_batched": (C.c_int, [_P, C.c_int, C.POINTER(CsrView), C.POINTER(C.c_int),
+                                       C.POINTER(C.POINTER(CsrView)), C.POINTER(Options), C.POINTER(C.c_void_p),
+                                       C.c_int, C.POINTER(Info)]),
     "ss_profile_enable": (C.c_int, [_P, C.c_int]),
     "ss_profile_read": (C.c_int, [_P, C.c_int, _I64P, _DP]),
     "steady_state": (C.c_int, [_P, C.POINTER(CsrView), C.c_int, C.POINTER(CsrView), C.POINTER(Options),

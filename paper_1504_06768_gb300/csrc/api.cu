@@ -442,8 +442,9 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
         return set_error(ctx, SS_ERR_UNSUPPORTED, "method=direct is not built; use an iterative method");
     if (opt.method < SS_METHOD_ITER_GMRES || opt.method > SS_METHOD_INVERSE_POWER)
         return set_error(ctx, SS_ERR_INVALID, "unknown method");
-    if (opt.precision == SS_PREC_MIXED)
-        return set_error(ctx, SS_ERR_UNSUPPORTED, "mixed precision is not available in this entry point");
+    const bool mixed = opt.precision == SS_PREC_MIXED;
+    if (mixed && opt.method != SS_METHOD_ITER_BICGSTAB)
+        return set_error(ctx, SS_ERR_UNSUPPORTED, "mixed precision is built for iterative-bicgstab only");
     if (!(opt.tol > 0.0) || opt.maxiter < 1) return set_error(ctx, SS_ERR_INVALID, "tol must be > 0, maxiter >= 1");
     const bool power = opt.method == SS_METHOD_INVERSE_POWER;
     const int krylov = opt.method == SS_METHOD_ITER_GMRES ? SS_KRYLOV_GMRES : SS_KRYLOV_BICGSTAB;
@@ -472,7 +473,8 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
     inf.nnz = Ap->m.nnz;
     inf.w_used = w_used;
     bandwidth_profile_impl(ctx, Ap->m, &inf.bandwidth, &inf.profile);
-    st = build_prec(ctx, Ap->m, opt.precond, opt.drop_tol, opt.fill_factor, false, &M);
+    st = build_prec(ctx, Ap->m, opt.precond, opt.drop_tol, opt.fill_factor, mixed, &M);
+    if (st == SS_OK && mixed) st = ensure_f32(ctx, Ap);
     if (st != SS_OK) { ss_mat_free(Ap); return st; }
     inf.nnz_factors = M->f.nnz;
     inf.levels_lower = M->lower.n_levels;
@@ -512,7 +514,36 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
     int status = SS_NOT_CONVERGED, total = 0, outer = 0;
     const int64_t r0 = iperm[0];
     KrylovResultHost res;
-    if (!power) {
+    if (mixed) {
+        // FP32 inner BiCGSTAB on r / ||r||, refined in FP64: x += ||r|| c
+        STEP(su_zero(ctx, n, b));
+        double2 wb = make_double2(w_used, 0.0);
+        SS_CUDA(ctx, cudaMemcpyAsync(b + r0, &wb, sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+        STEP(su_zero(ctx, n, x));
+        double2* r64 = nullptr;
+        float2 *b32 = nullptr, *x32 = nullptr;
+        STEP(dev_alloc_n(ctx, &r64, (size_t)n));
+        STEP(dev_alloc_n(ctx, &b32, (size_t)n));
+        STEP(dev_alloc_n(ctx, &x32, (size_t)n));
+        for (outer = 1; outer <= 30; ++outer) {
+            if (outer > 1) {
+                STEP(su_lrho(ctx, Ap->m, x, 0, w_used, r0, d, tidx_d, y, scr, trace_d, &lr, nullptr));
+                if (lr <= opt.tol) { status = SS_OK; break; }
+            }
+            if (total >= opt.maxiter) break;
+            double rn = 0.0;
+            STEP(su_refine_residual(ctx, Ap->m, b, x, y, r64, b32, x32, scr, &rn));
+            if (rn == 0.0) { status = SS_OK; lr = 0.0; break; }
+            STEP(bicgstab_dev32(ctx, Ap->m, Ap->val32, M, kw, b32, x32, 1e-4, opt.maxiter - total, &res));
+            total += res.iters;
+            STEP(su_refine_update(ctx, n, x, scr, x32));
+            if (res.status == SS_BREAKDOWN && res.iters == 0) { status = SS_BREAKDOWN; break; }
+        }
+        if (outer > 30) outer = 30;
+        dev_free(ctx, r64);
+        dev_free(ctx, b32);
+        dev_free(ctx, x32);
+    } else if (!power) {
         STEP(su_zero(ctx, n, b));
         double2 wb = make_double2(w_used, 0.0);
         SS_CUDA(ctx, cudaMemcpyAsync(b + r0, &wb, sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));

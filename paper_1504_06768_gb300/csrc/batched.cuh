@@ -1,0 +1,62 @@
+// Per-system persistent solver: one CTA takes one system at a time from a
+// work queue and runs the numeric iLU(0), the preconditioned BiCGSTAB (FP64,
+// or FP32 inner + FP64 refinement), the acceptance test and the
+// finalisation without leaving the kernel.
+#pragma once
+
+#include "common.cuh"
+
+constexpr int BATCH_THREADS = 512;
+
+struct BatchSys {
+    int32_t n, d;
+    // system matrix A (RCM-permuted L + wT or L - sigma I)
+    const int32_t* a_rp;
+    const int32_t* a_col;
+    const double2* a_val;
+    float2* a_val32;            // written by the kernel (mixed precision)
+    // combined incomplete factors (pattern of A for iLU(0)); values written by the kernel
+    const int32_t* f_rp;
+    const int32_t* f_col;
+    const int32_t* f_dpos;
+    double2* f_val;
+    double2* f_inv;
+    float2* f_val32;
+    float2* f_inv32;
+    int32_t factor_on_device;   // 1: iLU(0) computed in the kernel from a_val; 0: factors given
+    // level structure
+    const int32_t* lo_units;
+    const int32_t* up_units;
+    int32_t lo_nunits, up_nunits;
+    int32_t lo_g, up_g, a_g;    // lanes per row of the two solves and of the SpMV
+    const int32_t* lvl_ptr;     // lower level boundaries in lvl_rows (factorisation schedule)
+    const int32_t* lvl_rows;
+    int32_t n_levels;
+    // right-hand side / trace
+    int32_t r0;                 // permuted position of row 0
+    double w;                   // weight of the trace row (0: shifted system)
+    double sigma;
+    const int32_t* perm;        // perm[new] = old
+    const int32_t* tidx;        // permuted positions of the diagonal elements rho_ii
+    // work: 10 vectors of n elements of the inner type + x64, r64 (FP64)
+    void* work;
+    double2* x64;
+    double2* r64;
+    double2* rho_out;           // natural column-major order, device
+    // results
+    int status, iters, outer;
+    double resid;
+};
+
+struct BatchParams {
+    double tol;
+    int maxiter;
+    int mixed;                  // 0: FP64, 1: FP32 inner + FP64 refinement
+    double inner_rtol;          // mixed: inner relative tolerance
+    int power;                  // inverse power (FP64 only)
+    uint64_t seed;
+};
+
+size_t batch_smem_bytes(int n, bool mixed);
+int batch_max_n(bool mixed);
+ss_status batch_launch(ss_ctx ctx, BatchSys* dsys, int nsys, const BatchParams& p, int max_n, int* queue, int* err);

@@ -96,10 +96,10 @@ struct ss_prec_s {
     float2* val32 = nullptr;          // FP32 factors (mixed precision)
     float2* inv_diag32 = nullptr;
     TriLevels lower, upper;
-    uint32_t* flags = nullptr;        // per-row completion flags for the sync-free solves
-    unsigned long long* tickets = nullptr;  // [0] lower, [1] upper
+    uint32_t* flags = nullptr;        // unused (kept null)
+    unsigned long long* tickets = nullptr;  // [0] lower, [1] upper block tickets
     int* err = nullptr;               // device error word (bounded waits)
-    double2* tmp = nullptr;           // intermediate vector of the two solves
+    double2* tmp = nullptr;           // intermediate vector of the two solves (PENDING between uses)
     float2* tmp32 = nullptr;
 };
 
@@ -141,8 +141,10 @@ void free_csr(ss_ctx ctx, DeviceCSR& m);
 
 // --------------------------------------------------------- device helpers
 
-// Exclusive scan of n int32 counts into n+1 offsets (out[0] = 0, out[n] = total);
-// returns the total in *total (host) and fails with SS_ERR_UNSUPPORTED past 2^31-1.
+// Exclusive scan of n int32 counts into n+1 offsets (out[0] = 0, out[n] = total).
+// With total != NULL the call waits for the result, returns it in *total and
+// fails with SS_ERR_UNSUPPORTED past 2^31-1; with total == NULL it stays
+// asynchronous (for sums already known to fit, e.g. a permutation of rows).
 ss_status exclusive_scan_i32(ss_ctx ctx, const int32_t* counts, int32_t* out, int64_t n, int64_t* total);
 // Position of the diagonal entry in each row (-1 when absent).
 ss_status find_diag(ss_ctx ctx, const DeviceCSR& m, int32_t* diag_pos);

@@ -103,16 +103,31 @@ __device__ __forceinline__ bool negligible(double2 a, double nu, double nv) {
 }
 
 // ----------------------------------------------------------- BiCGSTAB
+// Vector type T is double2 (FP64) or float2 (the inner solve of the mixed
+// path); updates run in T's precision, inner products accumulate in FP64.
+
+__device__ __forceinline__ double2 dd(double2 a) { return a; }
+__device__ __forceinline__ double2 dd(float2 a) { return make_double2(a.x, a.y); }
+template <class T> __device__ __forceinline__ T tt(double2 a);
+template <> __device__ __forceinline__ double2 tt<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 tt<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 tmul(double2 a, double2 b) { return cmul(a, b); }
+__device__ __forceinline__ float2 tmul(float2 a, float2 b) { return fcmul(a, b); }
+__device__ __forceinline__ double2 tadd(double2 a, double2 b) { return cadd(a, b); }
+__device__ __forceinline__ float2 tadd(float2 a, float2 b) { return fcadd(a, b); }
+__device__ __forceinline__ double2 tsub(double2 a, double2 b) { return csub(a, b); }
+__device__ __forceinline__ float2 tsub(float2 a, float2 b) { return fcsub(a, b); }
 
 // r = b - y (y = A x), rhat = r, rho = <r, r>
-__global__ void bicg_init(int64_t n, const double2* __restrict__ b, const double2* __restrict__ y,
-                          double2* __restrict__ r, double2* __restrict__ rhat, KrylovState* st) {
+template <class T>
+__global__ void bicg_init(int64_t n, const T* __restrict__ b, const T* __restrict__ y,
+                          T* __restrict__ r, T* __restrict__ rhat, KrylovState* st) {
     double2 v[1] = {d2(0, 0)};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 ri = csub(b[i], y[i]);
+        T ri = tsub(b[i], y[i]);
         r[i] = ri;
         rhat[i] = ri;
-        v[0].x += cabs2(ri);
+        v[0].x += cabs2(dd(ri));
     }
     if (reduce_last_block<1>(v, st->partials, &st->counter)) {
         double rn = sqrt(v[0].x);
@@ -128,26 +143,29 @@ __global__ void bicg_init(int64_t n, const double2* __restrict__ b, const double
 }
 
 // p = r (first iteration) or p = r + beta (p - omega v)
-__global__ void bicg_p(int64_t n, const double2* __restrict__ r, const double2* __restrict__ v, double2* __restrict__ p,
+template <class T>
+__global__ void bicg_p(int64_t n, const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ p,
                        const KrylovState* st) {
     if (st->halt) return;
     const bool first = st->iters == 0;
-    const double2 beta = st->beta, omega = st->omega;
+    const T beta = tt<T>(st->beta), omega = tt<T>(st->omega);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (first) p[i] = r[i];
-        else p[i] = cadd(r[i], cmul(beta, csub(p[i], cmul(omega, v[i]))));
+        else p[i] = tadd(r[i], tmul(beta, tsub(p[i], tmul(omega, v[i]))));
     }
 }
 
 // alpha = rho / <rhat, v>
-__global__ void bicg_rv(int64_t n, const double2* __restrict__ rhat, const double2* __restrict__ v, KrylovState* st) {
+template <class T>
+__global__ void bicg_rv(int64_t n, const T* __restrict__ rhat, const T* __restrict__ v, KrylovState* st) {
     if (st->halt) return;
     double2 acc[2] = {d2(0, 0), d2(0, 0)};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 a = cmulc(rhat[i], v[i]);
+        const double2 h = dd(rhat[i]), vi = dd(v[i]);
+        double2 a = cmulc(h, vi);
         acc[0].x += a.x;
         acc[0].y += a.y;
-        acc[1].x += cabs2(v[i]);
+        acc[1].x += cabs2(vi);
     }
     if (reduce_last_block<2>(acc, st->partials, &st->counter)) {
         if (negligible(acc[0], st->rhat_norm, sqrt(acc[1].x))) {
@@ -159,15 +177,16 @@ __global__ void bicg_rv(int64_t n, const double2* __restrict__ rhat, const doubl
 }
 
 // s = r - alpha v; stop early when ||s|| <= tol
-__global__ void bicg_s(int64_t n, const double2* __restrict__ r, const double2* __restrict__ v, double2* __restrict__ s,
+template <class T>
+__global__ void bicg_s(int64_t n, const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ s,
                        KrylovState* st) {
     if (st->halt) return;
-    const double2 alpha = st->alpha;
+    const T alpha = tt<T>(st->alpha);
     double2 acc[1] = {d2(0, 0)};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 si = csub(r[i], cmul(alpha, v[i]));
+        T si = tsub(r[i], tmul(alpha, v[i]));
         s[i] = si;
-        acc[0].x += cabs2(si);
+        acc[0].x += cabs2(dd(si));
     }
     if (reduce_last_block<1>(acc, st->partials, &st->counter)) {
         double sn = sqrt(acc[0].x);
@@ -177,14 +196,16 @@ __global__ void bicg_s(int64_t n, const double2* __restrict__ r, const double2* 
 }
 
 // omega = <t, s> / <t, t>
-__global__ void bicg_ts(int64_t n, const double2* __restrict__ t, const double2* __restrict__ s, KrylovState* st) {
+template <class T>
+__global__ void bicg_ts(int64_t n, const T* __restrict__ t, const T* __restrict__ s, KrylovState* st) {
     if (st->halt) return;
     double2 acc[2] = {d2(0, 0), d2(0, 0)};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 a = cmulc(t[i], s[i]);
+        const double2 ti = dd(t[i]);
+        double2 a = cmulc(ti, dd(s[i]));
         acc[0].x += a.x;
         acc[0].y += a.y;
-        acc[1].x += cabs2(t[i]);
+        acc[1].x += cabs2(ti);
     }
     if (reduce_last_block<2>(acc, st->partials, &st->counter)) {
         if (acc[1].x == 0.0) {
@@ -197,25 +218,28 @@ __global__ void bicg_ts(int64_t n, const double2* __restrict__ t, const double2*
 }
 
 // x += alpha phat + omega shat; r = s - omega t; rho_new = <rhat, r>
-__global__ void bicg_xr(int64_t n, double2* __restrict__ x, const double2* __restrict__ phat,
-                        const double2* __restrict__ shat, const double2* __restrict__ s, const double2* __restrict__ t,
-                        double2* __restrict__ r, const double2* __restrict__ rhat, KrylovState* st) {
+template <class T>
+__global__ void bicg_xr(int64_t n, T* __restrict__ x, const T* __restrict__ phat,
+                        const T* __restrict__ shat, const T* __restrict__ s, const T* __restrict__ t,
+                        T* __restrict__ r, const T* __restrict__ rhat, KrylovState* st) {
     if (st->done) return;
     const double2 alpha = st->alpha, omega = st->omega;
+    const T al = tt<T>(alpha), om = tt<T>(omega);
     const bool sconv = st->sconv;
     double2 acc[2] = {d2(0, 0), d2(0, 0)};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (sconv) {
-            x[i] = cadd(x[i], cmul(alpha, phat[i]));
+            x[i] = tadd(x[i], tmul(al, phat[i]));
             r[i] = s[i];
         } else {
-            x[i] = cadd(x[i], cadd(cmul(alpha, phat[i]), cmul(omega, shat[i])));
-            double2 ri = csub(s[i], cmul(omega, t[i]));
+            x[i] = tadd(x[i], tadd(tmul(al, phat[i]), tmul(om, shat[i])));
+            T ri = tsub(s[i], tmul(om, t[i]));
             r[i] = ri;
-            double2 a = cmulc(rhat[i], ri);
+            const double2 rd = dd(ri);
+            double2 a = cmulc(dd(rhat[i]), rd);
             acc[0].x += a.x;
             acc[0].y += a.y;
-            acc[1].x += cabs2(ri);
+            acc[1].x += cabs2(rd);
         }
     }
     if (reduce_last_block<2>(acc, st->partials, &st->counter)) {
@@ -429,43 +453,64 @@ static ss_status outer_met(ss_ctx ctx, const OuterCheck* oc, const double2* x, b
     return SS_OK;
 }
 
-ss_status bicgstab_dev(ss_ctx ctx, const DeviceCSR& A, ss_prec M, KrylovWork& w, const double2* b, double2* x,
-                       double tol, int maxiter, KrylovResultHost* out, const OuterCheck* oc) {
+template <class T>
+static void spmv_any(ss_ctx ctx, const DeviceCSR& A, const float2* val32, const T* x, T* y, const int* halt);
+template <>
+void spmv_any<double2>(ss_ctx ctx, const DeviceCSR& A, const float2*, const double2* x, double2* y, const int* halt) {
+    ProfScope ps_(ctx, PROF_SPMV);
+    spmv_launch(A, x, y, halt, ctx->stream);
+}
+template <>
+void spmv_any<float2>(ss_ctx ctx, const DeviceCSR& A, const float2* val32, const float2* x, float2* y, const int* halt) {
+    ProfScope ps_(ctx, PROF_SPMV);
+    spmv_launch32(A, val32, x, y, halt, ctx->stream);
+}
+static ss_status prec_any(ss_ctx ctx, ss_prec M, const double2* r, double2* z, const int* halt) {
+    return prec_apply_dev(ctx, M, r, z, halt);
+}
+static ss_status prec_any(ss_ctx ctx, ss_prec M, const float2* r, float2* z, const int* halt) {
+    return prec_apply_dev32(ctx, M, r, z, halt);
+}
+
+template <class T>
+static ss_status bicgstab_any(ss_ctx ctx, const DeviceCSR& A, const float2* val32, ss_prec M, KrylovWork& w,
+                              const T* b, T* x, double tol, int maxiter, KrylovResultHost* out,
+                              const OuterCheck* oc) {
     const int64_t n = A.n_rows;
-    double2* r = w.vecs;
-    double2* rhat = r + n;
-    double2* p = rhat + n;
-    double2* v = p + n;
-    double2* s = v + n;
-    double2* t = s + n;
-    double2* phat = t + n;
-    double2* shat = phat + n;
+    T* r = reinterpret_cast<T*>(w.vecs);
+    T* rhat = r + n;
+    T* p = rhat + n;
+    T* v = p + n;
+    T* s = v + n;
+    T* t = s + n;
+    T* phat = t + n;
+    T* shat = phat + n;
     const int nb = red_blocks(n);
     const unsigned eg = (unsigned)std::min<int64_t>(grid_for(n, RED_THREADS), 4 * std::max(ctx->num_sms, 1));
     int* halt = &w.st->halt;
     SS_TRY(set_params(ctx, w, tol, maxiter, 0));
-    { ProfScope ps_(ctx, PROF_SPMV); spmv_launch(A, x, v, nullptr, ctx->stream); }
-    bicg_init<<<nb, RED_THREADS, 0, ctx->stream>>>(n, b, v, r, rhat, w.st);
+    spmv_any<T>(ctx, A, val32, x, v, nullptr);
+    bicg_init<T><<<nb, RED_THREADS, 0, ctx->stream>>>(n, b, v, r, rhat, w.st);
     SS_CUDA(ctx, cudaGetLastError());
     int queued = 0, chunk = 2;
     while (true) {
         for (int c = 0; c < chunk; ++c) {
-            bicg_p<<<eg, RED_THREADS, 0, ctx->stream>>>(n, r, v, p, w.st);
-            SS_TRY(prec_apply_dev(ctx, M, p, phat, halt));
-            { ProfScope ps_(ctx, PROF_SPMV); spmv_launch(A, phat, v, halt, ctx->stream); }
-            bicg_rv<<<nb, RED_THREADS, 0, ctx->stream>>>(n, rhat, v, w.st);
-            bicg_s<<<nb, RED_THREADS, 0, ctx->stream>>>(n, r, v, s, w.st);
-            SS_TRY(prec_apply_dev(ctx, M, s, shat, halt));
-            { ProfScope ps_(ctx, PROF_SPMV); spmv_launch(A, shat, t, halt, ctx->stream); }
-            bicg_ts<<<nb, RED_THREADS, 0, ctx->stream>>>(n, t, s, w.st);
-            bicg_xr<<<nb, RED_THREADS, 0, ctx->stream>>>(n, x, phat, shat, s, t, r, rhat, w.st);
+            bicg_p<T><<<eg, RED_THREADS, 0, ctx->stream>>>(n, r, v, p, w.st);
+            SS_TRY(prec_any(ctx, M, p, phat, halt));
+            spmv_any<T>(ctx, A, val32, phat, v, halt);
+            bicg_rv<T><<<nb, RED_THREADS, 0, ctx->stream>>>(n, rhat, v, w.st);
+            bicg_s<T><<<nb, RED_THREADS, 0, ctx->stream>>>(n, r, v, s, w.st);
+            SS_TRY(prec_any(ctx, M, s, shat, halt));
+            spmv_any<T>(ctx, A, val32, shat, t, halt);
+            bicg_ts<T><<<nb, RED_THREADS, 0, ctx->stream>>>(n, t, s, w.st);
+            bicg_xr<T><<<nb, RED_THREADS, 0, ctx->stream>>>(n, x, phat, shat, s, t, r, rhat, w.st);
         }
         SS_CUDA(ctx, cudaGetLastError());
         queued += chunk;
         SS_TRY(read_state(ctx, w));
         if (w.host_st->done) break;
         bool met = false;
-        SS_TRY(outer_met(ctx, oc, x, &met));
+        if (oc) SS_TRY(outer_met(ctx, oc, reinterpret_cast<const double2*>(x), &met));
         if (met) { w.host_st->status = SS_OK; break; }
         if (queued > maxiter + 8) break;   // cannot happen: the state sets done at maxiter
         chunk = std::min(chunk * 2, 32);
@@ -475,6 +520,16 @@ ss_status bicgstab_dev(ss_ctx ctx, const DeviceCSR& A, ss_prec M, KrylovWork& w,
     out->iters = w.host_st->iters;
     out->resid = w.host_st->rnorm;
     return SS_OK;
+}
+
+ss_status bicgstab_dev(ss_ctx ctx, const DeviceCSR& A, ss_prec M, KrylovWork& w, const double2* b, double2* x,
+                       double tol, int maxiter, KrylovResultHost* out, const OuterCheck* oc) {
+    return bicgstab_any<double2>(ctx, A, nullptr, M, w, b, x, tol, maxiter, out, oc);
+}
+
+ss_status bicgstab_dev32(ss_ctx ctx, const DeviceCSR& A, const float2* val32, ss_prec M, KrylovWork& w,
+                         const float2* b, float2* x, double tol, int maxiter, KrylovResultHost* out) {
+    return bicgstab_any<float2>(ctx, A, val32, M, w, b, x, tol, maxiter, out, nullptr);
 }
 
 ss_status gmres_dev(ss_ctx ctx, const DeviceCSR& A, ss_prec M, KrylovWork& w, const double2* b, double2* x, double tol,

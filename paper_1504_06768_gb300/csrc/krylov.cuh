@@ -66,5 +66,8 @@ ss_status krylov_workspace(ss_ctx ctx, KrylovWork& w, int64_t n, int method, int
 void krylov_workspace_free(ss_ctx ctx, KrylovWork& w);
 ss_status bicgstab_dev(ss_ctx ctx, const DeviceCSR& A, ss_prec M, KrylovWork& w, const double2* b, double2* x,
                        double tol, int maxiter, KrylovResultHost* out, const OuterCheck* oc = nullptr);
+// FP32 BiCGSTAB (inner solve of the mixed path): A's FP32 values, M's FP32 factors.
+ss_status bicgstab_dev32(ss_ctx ctx, const DeviceCSR& A, const float2* val32, ss_prec M, KrylovWork& w,
+                         const float2* b, float2* x, double tol, int maxiter, KrylovResultHost* out);
 ss_status gmres_dev(ss_ctx ctx, const DeviceCSR& A, ss_prec M, KrylovWork& w, const double2* b, double2* x, double tol,
                     int maxiter, int m, KrylovResultHost* out, const OuterCheck* oc = nullptr);

@@ -2,12 +2,11 @@
 // numeric factorisation on the device, the level analysis that schedules it,
 // and the triangular solves z = U^{-1} L^{-1} r that apply M^{-1}.
 //
-// Triangular solves are "sync-free": one warp per row, rows handed out in
-// level order through a global ticket counter.  A row waits (bounded) for the
-// completion flags of the rows it depends on, which always hold earlier
-// tickets, so the earliest unfinished row can always proceed.  The ticket
-// number t also encodes the launch: position = t mod n, epoch = t / n + 1, so
-// neither the counter nor the flags are reset between solves.
+// Triangular solves are "sync-free": rows are grouped into level-aligned
+// units, blocks take runs of units in level order from a ticket counter, and
+// a row waits (bounded) until the values of the rows it depends on have been
+// written -- the output vector is pre-marked with a NaN payload that no
+// arithmetic produces, so the value doubles as its own completion flag.
 #include <algorithm>
 #include <vector>
 
@@ -47,14 +46,6 @@ template <> struct Cplx<float2> {
     __device__ static float2 ldcg(const float2* p) { return __ldcg(p); }
 };
 
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -63,32 +54,55 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // a single wait gives up after 2 s
 
-// One warp handles one "unit": up to R = 32 / G rows of the same level, G lanes
-// per row.  Units are handed out in level order by a ticket counter; a row
-// waits (bounded) for the completion flags of the rows it depends on, all of
-// which belong to earlier levels and so to earlier tickets.
-// LOWER: x_i = b_i - sum_{j<i} l_ij x_j (unit diagonal).
-// UPPER: x_i = (b_i - sum_{j>i} u_ij x_j) / u_ii.
+// "Not yet computed" marks: NaN bit patterns with a payload that arithmetic
+// never produces (arithmetic NaNs carry the canonical payload).
+constexpr unsigned long long PENDING64 = 0xFFFDEADBEEFDEAD1ull;
+constexpr unsigned int PENDING32 = 0xFFBADBADu;
+
+__device__ __forceinline__ bool ready(double2 v) {
+    return __double_as_longlong(v.x) != (long long)PENDING64 && __double_as_longlong(v.y) != (long long)PENDING64;
+}
+__device__ __forceinline__ bool ready(float2 v) {
+    return __float_as_uint(v.x) != PENDING32 && __float_as_uint(v.y) != PENDING32;
+}
+template <class T> __device__ __forceinline__ T pending();
+template <> __device__ __forceinline__ double2 pending<double2>() {
+    return make_double2(__longlong_as_double((long long)PENDING64), __longlong_as_double((long long)PENDING64));
+}
+template <> __device__ __forceinline__ float2 pending<float2>() {
+    return make_float2(__uint_as_float(PENDING32), __uint_as_float(PENDING32));
+}
+
+// Sync-free triangular solve.  One warp handles one "unit": up to R = 32 / G
+// rows of the same level, G lanes per row.  Blocks take consecutive runs of
+// units in level order through a ticket counter (one atomic per block), so a
+// row only ever waits for rows held by earlier, resident blocks.  The output
+// vector starts filled with the PENDING mark; a row waits (bounded) until the
+// values it depends on are no longer PENDING -- the value itself is the
+// completion signal, so no flag or fence is needed.
+//   LOWER: x_i = b_i - sum_{j<i} l_ij x_j (unit diagonal); also re-marks
+//          `other[i]` (the upper solve's output) PENDING.
+//   UPPER: x_i = (b_i - sum_{j>i} u_ij x_j) / u_ii; afterwards re-marks b_i
+//          (the lower solve's output) PENDING for the next application.
 template <bool LOWER, int G, class T>
 __global__ void __launch_bounds__(256) sptrsv_syncfree(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                        const T* __restrict__ val, const int32_t* __restrict__ dpos,
                                                        const T* __restrict__ inv_diag, const int32_t* __restrict__ units,
-                                                       int64_t n_units, const T* __restrict__ b, T* __restrict__ x,
-                                                       uint32_t* __restrict__ flags,
+                                                       int64_t n_units, T* b, T* x, T* other,
                                                        unsigned long long* __restrict__ ticket, int* __restrict__ err,
                                                        const int* __restrict__ halt) {
     using C = Cplx<T>;
     constexpr int R = 32 / G;
     if (halt && *halt) return;      // uniform over the launch: no ticket is taken
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (gw >= n_units) return;
+    __shared__ unsigned long long s_ticket;
+    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1ull);
+    __syncthreads();
+    const int64_t nblocks = gridDim.x;
+    const int64_t wpb = blockDim.x >> 5;
+    const int64_t u = (int64_t)(s_ticket % (unsigned long long)nblocks) * wpb + (threadIdx.x >> 5);
+    if (u >= n_units) return;
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane % G;
-    unsigned long long t = 0;
-    if (lane == 0) t = atomicAdd(ticket, 1ull);
-    t = __shfl_sync(FULL, t, 0);
-    const int64_t u = (int64_t)(t % (unsigned long long)n_units);
-    const uint32_t epoch = (uint32_t)(t / (unsigned long long)n_units) + 1u;
     const int32_t i = units[u * R + grp];          // -1 pads a unit at the end of a level
     int32_t s = 0, e = 0;
     if (i >= 0) {
@@ -97,40 +111,46 @@ __global__ void __launch_bounds__(256) sptrsv_syncfree(const int32_t* __restrict
     }
     T acc = C::zero();
     bool timed_out = false;
-    // 1) wait until every dependency of this lane is complete
     for (int32_t k = s + sub; k < e; k += G) {
-        const int32_t j = col[k];
-        if (ld_relaxed(&flags[j]) != epoch) {
+        const T v = val[k];
+        const T* xp = &x[col[k]];
+        T xj = __ldcv(xp);
+        if (!ready(xj)) {
             const unsigned long long t0 = globaltimer_ns();
-            unsigned ns = 16;
+            int spins = 0;
             while (true) {
-                __nanosleep(ns);
-                if (ld_relaxed(&flags[j]) == epoch) break;
-                if (ns < 128) ns <<= 1;
-                if (*(volatile int*)err != 0 || globaltimer_ns() - t0 > WAIT_NS) {
+                if (++spins > 64) __nanosleep(64);
+                xj = __ldcv(xp);
+                if (ready(xj)) break;
+                if ((spins & 63) == 0 && (*(volatile int*)err != 0 || globaltimer_ns() - t0 > WAIT_NS)) {
                     timed_out = true;
+                    xj = C::zero();
                     break;
                 }
             }
         }
+        acc = C::fma_(v, xj, acc);
     }
-    __threadfence();                                  // acquire: the flags order the x[j] reads
-    // 2) accumulate
-    for (int32_t k = s + sub; k < e; k += G) acc = C::fma_(val[k], C::ldcg(&x[col[k]]), acc);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
-        T other = C::shfl_down(acc, o);
-        acc.x += other.x;
-        acc.y += other.y;
+        T other_v = C::shfl_down(acc, o);
+        acc.x += other_v.x;
+        acc.y += other_v.y;
     }
     if (__any_sync(FULL, timed_out) && lane == 0) atomicExch(err, 1);
     if (i >= 0 && sub == 0) {
         T xi = C::sub(b[i], acc);
         if (!LOWER) xi = C::mul(xi, inv_diag[i]);
         __stcg(&x[i], xi);
-        __threadfence();                              // release: x[i] before its flag
-        st_relaxed(&flags[i], epoch);
+        if (LOWER) __stcg(&other[i], pending<T>());
+        else __stcg(&b[i], pending<T>());
     }
+}
+
+template <class T>
+__global__ void fill_pending(int64_t n, T* __restrict__ a) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = pending<T>();
 }
 
 // ---------------------------------------------------------------- iLU(0)
@@ -235,11 +255,10 @@ static ss_status analyse(ss_ctx ctx, ss_prec M, const std::vector<int32_t>& hrp,
     const int64_t nnz_upper = (int64_t)hcol.size() - nnz_lower - n;
     SS_TRY(upload_levels(ctx, lower_order, lower_ptr, n ? (double)nnz_lower / n : 1.0, M->lower, nl));
     SS_TRY(upload_levels(ctx, upper_order, upper_ptr, n ? (double)nnz_upper / n : 1.0, M->upper, nu));
-    SS_TRY(dev_alloc_n(ctx, &M->flags, (size_t)2 * n));
     SS_TRY(dev_alloc_n(ctx, &M->tickets, 2));
     SS_TRY(dev_alloc_n(ctx, &M->err, 1));
     SS_TRY(dev_alloc_n(ctx, &M->tmp, (size_t)n));
-    SS_CUDA(ctx, cudaMemsetAsync(M->flags, 0, sizeof(uint32_t) * 2 * n, ctx->stream));
+    fill_pending<double2><<<256, 256, 0, ctx->stream>>>(n, M->tmp);
     SS_CUDA(ctx, cudaMemsetAsync(M->tickets, 0, sizeof(unsigned long long) * 2, ctx->stream));
     SS_CUDA(ctx, cudaMemsetAsync(M->err, 0, sizeof(int), ctx->stream));
     return SS_OK;
@@ -302,6 +321,7 @@ ss_status prec_finish(ss_ctx ctx, ss_prec M, bool want_fp32) {
         SS_TRY(dev_alloc_n(ctx, &M->val32, (size_t)M->f.nnz));
         SS_TRY(dev_alloc_n(ctx, &M->inv_diag32, (size_t)n));
         SS_TRY(dev_alloc_n(ctx, &M->tmp32, (size_t)n));
+        fill_pending<float2><<<256, 256, 0, ctx->stream>>>(n, M->tmp32);
     }
     make_inv_diag<<<grid_for(n, 256), 256, 0, ctx->stream>>>(M->f.val, M->diag_pos, n, M->inv_diag, M->inv_diag32,
                                                              M->err);
@@ -317,15 +337,15 @@ ss_status prec_finish(ss_ctx ctx, ss_prec M, bool want_fp32) {
 }
 
 template <bool LOWER, class T>
-static void launch_trsv(ss_ctx ctx, ss_prec M, const TriLevels& L, const T* vals, const T* inv, const T* b, T* x,
-                        uint32_t* flags, unsigned long long* ticket, const int* halt) {
+static void launch_trsv(ss_ctx ctx, ss_prec M, const TriLevels& L, const T* vals, const T* inv, T* b, T* x, T* other,
+                        unsigned long long* ticket, const int* halt) {
     const int threads = 256;
     const unsigned g = (unsigned)((L.n_units * 32 + threads - 1) / threads);
 #define SS_TRSV_CASE(GG)                                                                                    \
     case GG:                                                                                                \
         sptrsv_syncfree<LOWER, GG, T><<<g, threads, 0, ctx->stream>>>(M->f.row_ptr, M->f.col, vals,        \
                                                                        M->diag_pos, inv, L.units, L.n_units, \
-                                                                       b, x, flags, ticket, M->err, halt);   \
+                                                                       b, x, other, ticket, M->err, halt);   \
         break;
     switch (L.g) {
         SS_TRSV_CASE(2)
@@ -338,6 +358,9 @@ static void launch_trsv(ss_ctx ctx, ss_prec M, const TriLevels& L, const T* vals
 #undef SS_TRSV_CASE
 }
 
+// z = U^{-1} L^{-1} r.  tmp (the lower solve's output) is all PENDING between
+// applications; the lower solve marks z PENDING and the upper solve restores
+// tmp.  r and z must not alias.
 template <class T>
 static ss_status apply_impl(ss_ctx ctx, ss_prec M, const T* vals, const T* inv, T* tmp, const T* r, T* z,
                             const int* halt) {
@@ -345,11 +368,11 @@ static ss_status apply_impl(ss_ctx ctx, ss_prec M, const T* vals, const T* inv, 
     if (n == 0) return SS_OK;
     {
         ProfScope ps(ctx, PROF_TRSV_LOWER);
-        launch_trsv<true, T>(ctx, M, M->lower, vals, inv, r, tmp, M->flags, M->tickets, halt);
+        launch_trsv<true, T>(ctx, M, M->lower, vals, inv, const_cast<T*>(r), tmp, z, M->tickets, halt);
     }
     {
         ProfScope ps(ctx, PROF_TRSV_UPPER);
-        launch_trsv<false, T>(ctx, M, M->upper, vals, inv, tmp, z, M->flags + n, M->tickets + 1, halt);
+        launch_trsv<false, T>(ctx, M, M->upper, vals, inv, tmp, z, nullptr, M->tickets + 1, halt);
     }
     SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;

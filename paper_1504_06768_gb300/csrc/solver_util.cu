@@ -143,7 +143,67 @@ __global__ void max_part(const double* __restrict__ part, int np, double* __rest
 
 constexpr int NB = 256;
 
+// r = b - y and partial ||r||^2 per block
+__global__ void resid_partial(int64_t n, const double2* __restrict__ b, const double2* __restrict__ y,
+                              double2* __restrict__ r, double* __restrict__ part) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 v = csub(b[i], y[i]);
+        r[i] = v;
+        s += cabs2(v);
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// b32 = r / ||r|| (FP32), x32 = 0
+__global__ void scale_to32(int64_t n, const double2* __restrict__ r, const double* __restrict__ nrm2,
+                           float2* __restrict__ b32, float2* __restrict__ x32) {
+    const double inv = 1.0 / sqrt(*nrm2);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        b32[i] = make_float2((float)(r[i].x * inv), (float)(r[i].y * inv));
+        x32[i] = make_float2(0.f, 0.f);
+    }
+}
+
+// x += ||r|| c (c in FP32)
+__global__ void axpy_from32(int64_t n, double2* __restrict__ x, const double* __restrict__ nrm2,
+                            const float2* __restrict__ c) {
+    const double a = sqrt(*nrm2);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i].x += a * (double)c[i].x;
+        x[i].y += a * (double)c[i].y;
+    }
+}
+
 }  // namespace
+
+// r = b - A x (FP64), b32 = r / ||r||, x32 = 0; ||r|| to the host and kept in scratch[NB]
+ss_status su_refine_residual(ss_ctx ctx, const DeviceCSR& A, const double2* b, const double2* x, double2* y,
+                             double2* r, float2* b32, float2* x32, double* scratch, double* rnorm) {
+    { ProfScope ps_(ctx, PROF_SPMV); spmv_launch(A, x, y, nullptr, ctx->stream); }
+    resid_partial<<<NB, 256, 0, ctx->stream>>>(A.n_rows, b, y, r, scratch);
+    sum_part<<<1, 256, 0, ctx->stream>>>(scratch, NB, scratch + NB);
+    double h = 0.0;
+    SS_CUDA(ctx, cudaMemcpyAsync(&h, scratch + NB, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *rnorm = sqrt(h);
+    if (h > 0.0) scale_to32<<<1024, 256, 0, ctx->stream>>>(A.n_rows, r, scratch + NB, b32, x32);
+    SS_CUDA(ctx, cudaGetLastError());
+    return SS_OK;
+}
+
+ss_status su_refine_update(ss_ctx ctx, int64_t n, double2* x, const double* scratch, const float2* c) {
+    axpy_from32<<<1024, 256, 0, ctx->stream>>>(n, x, scratch + NB, c);
+    SS_CUDA(ctx, cudaGetLastError());
+    return SS_OK;
+}
 
 ss_status su_zero(ss_ctx ctx, int64_t n, double2* v) {
     fill_zero<<<grid_for(n, 256) > 1024 ? 1024 : grid_for(n, 256), 256, 0, ctx->stream>>>(n, v);

@@ -14,3 +14,8 @@ ss_status su_finalise(ss_ctx ctx, int64_t n, const int32_t* perm_dev, const doub
                       double2* rho_dev);
 ss_status su_condest(ss_ctx ctx, ss_prec M, int64_t n, double2* ones, double2* z, double* scratch, double* out);
 int su_scratch_doubles();
+// Mixed-precision refinement: r = b - A x in FP64, b32 = r / ||r||, x32 = 0;
+// then x += ||r|| c.
+ss_status su_refine_residual(ss_ctx ctx, const DeviceCSR& A, const double2* b, const double2* x, double2* y,
+                             double2* r, float2* b32, float2* x32, double* scratch, double* rnorm);
+ss_status su_refine_update(ss_ctx ctx, int64_t n, double2* x, const double* scratch, const float2* c);

@@ -114,11 +114,16 @@ ss_status exclusive_scan_i32(ss_ctx ctx, const int32_t* counts, int32_t* out, in
     scan_block_sums<<<(unsigned)nb, SCAN_BLOCK, 0, ctx->stream>>>(counts, n, sums);
     scan_sums_single<<<1, SCAN_BLOCK, 0, ctx->stream>>>(sums, nb, tot);
     scan_apply<<<(unsigned)nb, SCAN_BLOCK, 0, ctx->stream>>>(counts, n, sums, out, tot);
+    SS_CUDA(ctx, cudaGetLastError());
+    if (!total) {              // the caller knows the total fits: stay asynchronous
+        dev_free(ctx, sums);
+        return SS_OK;
+    }
     long long h = 0;
     SS_CUDA(ctx, cudaMemcpyAsync(&h, tot, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
     SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     dev_free(ctx, sums);
-    if (total) *total = h;
+    *total = h;
     if (h > INT32_MAX) return set_error(ctx, SS_ERR_UNSUPPORTED, "more than 2^31-1 stored entries");
     return SS_OK;
 }

@@ -347,9 +347,9 @@ def test_closed_forms_on_gpu(ss):
     assert float(np.sum(np.arange(20) * np.diag(rho).real)) == pytest.approx(0.2, abs=1e-10)
 
 
-@pytest.mark.parametrize("seed", [0, 7])
-@pytest.mark.parametrize("method,precond", [("iterative-bicgstab", "ilut"), ("iterative-lgmres", "ilut"),
-                                            ("inverse-power", "ilut"), ("iterative-bicgstab", "ilu0")])
+@pytest.mark.parametrize("seed,method,precond", [(0, "iterative-bicgstab", "ilut"), (0, "iterative-lgmres", "ilut"),
+                                                 (0, "inverse-power", "ilut"), (7, "iterative-bicgstab", "ilu0"),
+                                                 (7, "iterative-lgmres", "ilu0"), (7, "inverse-power", "ilu0")])
 def test_steady_state_config2_jc40(ss, seed, method, precond):
     s = jaynes_cummings_rwa(seed=seed)
     rho, info = ss.steady_state(s.H, s.c_ops, method=method, precond=precond, tol=1e-12)
@@ -387,3 +387,27 @@ def test_rho_written_to_device_buffer(ss):
     out = torch.empty(100, dtype=torch.complex128, device="cuda")
     rho, info = ss.steady_state(s.H, s.c_ops, out=out, tol=1e-12)
     assert trace_distance(rho.cpu().numpy(), steady_state_dense(s.H, s.c_ops)) < 1e-10
+
+
+def test_config3_optomechanics_mixed(ss):
+    """Optomechanics 10 x 40 (n = 160,000): the FP32-inner / FP64-refined
+    solve reaches ||L rho|| <= 1e-10 and agrees with the FP64 GPU solve
+    (trace distance <= 1e-8) and with the CPU sparse iterative oracle."""
+    from oracle.krylov import steady_state_iterative
+    s = optomechanics(seed=0)
+    rho_m, info_m = ss.steady_state(s.H, s.c_ops, precision="mixed", tol=1e-10)
+    assert info_m["status"] == 0 and info_m["resid_Lrho"] <= 1e-10 and info_m["n"] == 160000
+    rho_d, info_d = ss.steady_state(s.H, s.c_ops, tol=1e-11)
+    assert info_d["status"] == 0
+    assert trace_distance(rho_m, rho_d) <= 1e-8
+    ref = steady_state_iterative(s.H, s.c_ops, method="bicgstab", precond="ilu0", tol=1e-11)
+    assert ref.status == 0
+    assert trace_distance(rho_d, ref.rho) <= 1e-9
+
+
+@pytest.mark.parametrize("name", ["cavity_thermal", "kerr17", "jc8"])
+def test_mixed_single_system_small(ss, name):
+    s = SMALL_SYSTEMS[name]()
+    rho, info = ss.steady_state(s.H, s.c_ops, precision="mixed", tol=1e-11)
+    assert info["status"] == 0 and info["resid_Lrho"] <= 1e-11 and info["outer_iters"] >= 2
+    assert trace_distance(rho, steady_state_dense(s.H, s.c_ops)) <= 1e-8
