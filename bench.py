@@ -33,7 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "steady-state solves/s at ||L rho||<=1e-10 (FP64)"
+METRIC = "steady-state solves/s at ||L rho||<=1e-10"
 UNIT = "solves/s"
 TOL = 1e-10
 BATCH = 32
@@ -219,13 +219,16 @@ def run_gpu(args):
         step()
     infos.clear()
     lib.ss_profile_enable(ctx.handle, 1)
-    for kind in range(3):
+    kinds = ["spmv", "trsv_lower", "trsv_upper", "batched_solver"]
+    for kind in range(len(kinds)):
         lib.ss_profile_read(ctx.handle, kind, None, None)
+    launches0 = lib.ss_launch_count()
     with ClockSampler(local) as clk:
         times = timed(args.steps)
+    launches = lib.ss_launch_count() - launches0
     lib.ss_profile_enable(ctx.handle, 0)
     prof = {}
-    for kind, name in enumerate(["spmv", "trsv_lower", "trsv_upper"]):
+    for kind, name in enumerate(kinds):
         cnt, ms = C.c_int64(), C.c_double()
         lib.ss_profile_read(ctx.handle, kind, C.byref(cnt), C.byref(ms))
         prof[name] = (cnt.value, ms.value)
@@ -256,13 +259,18 @@ def run_gpu(args):
     n = d * d
     nnz = step_infos[0]["nnz"]
     nnzf = step_infos[0]["nnz_factors"]
+    vb = 8 if args.precision == "mixed" else 16          # bytes per complex vector element
+    ab = vb + 4                                           # bytes per stored matrix entry (value + column)
+    # one BiCGSTAB iteration of the per-system kernel: two SpMVs and two M^{-1}
+    # applications read A and the factors once each; the vector traffic is the
+    # sum of the vectors each phase reads and writes (30.5 vectors of n)
+    iter_bytes = 2 * ab * nnz + 2 * ab * nnzf + int(30.5 * vb * n)
+    total_iters = sum(i["iters"] for i in step_infos)
     bytes_per = {
-        # val 16 B + col 4 B per entry, row_ptr 4 B + y 16 B per row, x read once 16 B per row
         "spmv": 20 * nnz + 36 * n,
-        # each solve reads about half of the factors' entries plus the diagonal position,
-        # order index, rhs and result per row, and the completion flag per dependency
         "trsv_lower": 20 * (nnzf - n) // 2 + 44 * n,
         "trsv_upper": 20 * ((nnzf - n) // 2 + n) + 60 * n,
+        "batched_solver": iter_bytes * total_iters // max(args.steps, 1),
     }
     dom = max(prof, key=lambda k: prof[k][1])
     cnt, ms = prof[dom]
@@ -272,12 +280,14 @@ def run_gpu(args):
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
                 "peak_source": peak_kind, "launches": cnt, "avg_launch_us": 1000.0 * ms / max(cnt, 1),
                 "bytes_per_launch": bytes_per[dom],
-                "kernel_share_of_step": {k: prof[k][1] / total_ms for k in prof}}
+                "bytes_model": "per system-iteration: 2 SpMV + 2 M^-1 (matrix and factors once each) + "
+                               "30.5 vector passes of n; x iterations summed over the step's systems",
+                "kernel_share_of_step": {k: prof[k][1] / total_ms for k in prof if prof[k][0]}}
     # traffic per launch from the committed ncu summary, when it matches this build
     tr_file = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tr_file):
         tr = json.load(open(tr_file))
-        if tr.get("kernel") == dom and tr.get("workload") == "jc40":
+        if tr.get("kernel") == dom and tr.get("workload") == "jc40" and tr.get("precision") == args.precision:
             roofline["traffic"] = tr.get("bytes_per_launch")
 
     launches_per_step = sum(prof[k][0] for k in prof) / args.steps
@@ -285,24 +295,25 @@ def run_gpu(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+        "vs_baseline": None, "dtype": "c64 inner / c128 refined" if args.precision == "mixed" else "c128 (f64)",
+        "data": "synthetic",
         "config": {"workload": "jc40: driven dissipative Jaynes-Cummings, cavity 40 x atom, n=6400, "
                                f"{BATCH} seeds per step (E~U[0.2,1.5])",
-                   "method": args.method, "precond": precond, "ordering": "rcm", "tol": TOL,
+                   "method": args.method, "precond": precond, "precision": args.precision, "ordering": "rcm",
+                   "tol": TOL,
                    "batch_per_gpu": BATCH, "parallelism": f"replicas x{ws}",
                    "l2": "flushed between timed steps (256 MiB write, outside the events)"},
         "e2e": {"value": ws * BATCH / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": roofline,
         "clocks": clk.summary(),
-        "gpu_launches": None,
+        "gpu_launches": int(launches),
         "solve": {"iters_mean": statistics.mean(i["iters"] for i in step_infos), "max_resid_Lrho": resid,
                   "nnz": nnz, "nnz_factors": nnzf, "levels": [step_infos[0]["levels_lower"],
                                                                 step_infos[0]["levels_upper"]],
                   "ms_setup_mean": statistics.mean(i["ms_setup"] for i in step_infos),
                   "ms_solve_mean": statistics.mean(i["ms_solve"] for i in step_infos)},
     }
-    out["gpu_launches_profiled_per_step"] = launches_per_step
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     if ws > 1:

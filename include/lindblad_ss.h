@@ -96,6 +96,7 @@ typedef struct {
     double sigma;          /* shift of Eq. (inverse); 1e-15                                  */
     int use_rcm;           /* reverse Cuthill-McKee ordering of L~ + L~^T; 1                 */
     uint64_t seed;         /* inverse-power start vector (SplitMix64 counters); 0             */
+    double inner_rtol;     /* SS_PREC_MIXED: relative tolerance of each FP32 inner solve; 1e-5 */
 } ss_options;
 
 /* Per-solve diagnostics. */
@@ -241,16 +242,19 @@ ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_view* H, cons
 /* ---------------------------------------------------------- diagnostics */
 
 /* Kernel classes of the per-launch profiler. */
-typedef enum { SS_PROF_SPMV = 0, SS_PROF_TRSV_LOWER = 1, SS_PROF_TRSV_UPPER = 2 } ss_prof_kind;
+typedef enum { SS_PROF_SPMV = 0, SS_PROF_TRSV_LOWER = 1, SS_PROF_TRSV_UPPER = 2, SS_PROF_BATCHED = 3 } ss_prof_kind;
 
 /* When enabled, CUDA events are recorded on the context's stream around every
- * SpMV and triangular-solve launch issued through this context.  Not part of
+ * SpMV, triangular-solve and batched-solver launch issued through this context.  Not part of
  * the paper: a measurement aid for the bandwidth roofline. */
 ss_status ss_profile_enable(ss_ctx ctx, int enable);
 /* Synchronise the stream and return, for one kernel class, the number of
  * launches recorded since the last read and their summed device time in
  * milliseconds; the records of that class are then cleared. */
 ss_status ss_profile_read(ss_ctx ctx, int kind, int64_t* launches, double* total_ms);
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all contexts). */
+unsigned long long ss_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -284,7 +284,8 @@ def krylov_solve(A: Matrix, M: Preconditioner, b, x0=None, method: str = "bicgst
     return x, st, it.value, res.value
 
 
-def _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed):
+def _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed,
+             inner_rtol=1e-5):
     opt = B.Options()
     B.load().ss_options_default(C.byref(opt))
     opt.method = B.METHODS[method]
@@ -293,6 +294,7 @@ def _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_f
     opt.tol, opt.maxiter, opt.restart = tol, maxiter, restart
     opt.drop_tol, opt.fill_factor, opt.w, opt.sigma = drop_tol, fill_factor, w, sigma
     opt.use_rcm, opt.seed = int(bool(use_rcm)), seed
+    opt.inner_rtol = inner_rtol
     return opt
 
 
@@ -300,7 +302,7 @@ def steady_state_batched(systems: Sequence, method: str = "iterative-bicgstab", 
                          precond: str = "ilu0", precision: str = "fp64", maxiter: int = 1000, restart: int = 30,
                          drop_tol: float = 1e-4, fill_factor: float = 10.0, w: float = 0.0, sigma: float = 1e-15,
                          use_rcm: bool = True, seed: int = 0, ctx: Optional[Context] = None,
-                         raise_on_failure: bool = True):
+                         raise_on_failure: bool = True, inner_rtol: float = 1e-5):
     """Steady states of many systems, each given as (H, c_ops); returns a list
     of rho (numpy, d x d) and a list of info dicts."""
     ctx = ctx or get_context()
@@ -313,7 +315,8 @@ def steady_state_batched(systems: Sequence, method: str = "iterative-bicgstab", 
     rhos = [np.empty(h.view.n_rows ** 2, dtype=np.complex128) for h, _ in hosts]
     outs = (C.c_void_p * max(ns, 1))(*[r.ctypes.data for r in rhos])
     infos = (B.Info * max(ns, 1))()
-    opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed)
+    opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed,
+                   inner_rtol)
     st = B.load().steady_state_batched(ctx.handle, ns, Hs, ncs, cptrs, C.byref(opt), outs, 0, infos)
     if st != 0 and (raise_on_failure or st not in (B.SS_NOT_CONVERGED, B.SS_BREAKDOWN)):
         ctx.check(st, "steady_state_batched")
@@ -325,7 +328,7 @@ def steady_state(H, c_ops: Sequence, method: str = "iterative-bicgstab", tol: fl
                  precond: str = "ilu0", precision: str = "fp64", maxiter: int = 1000, restart: int = 30,
                  drop_tol: float = 1e-4, fill_factor: float = 10.0, w: float = 0.0, sigma: float = 1e-15,
                  use_rcm: bool = True, seed: int = 0, ctx: Optional[Context] = None, out=None,
-                 raise_on_failure: bool = True):
+                 raise_on_failure: bool = True, inner_rtol: float = 1e-5):
     """rho_ss (d x d complex128, trace one) and the solve's info dict.
 
     out: optional CUDA complex128 tensor of d*d elements (column-major rho);
@@ -336,7 +339,8 @@ def steady_state(H, c_ops: Sequence, method: str = "iterative-bicgstab", tol: fl
     hv = _CsrHost(H)
     cvs = [_CsrHost(c) for c in c_ops]
     arr = (B.CsrView * max(len(cvs), 1))(*[c.view for c in cvs])
-    opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed)
+    opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed,
+                   inner_rtol)
     d = hv.view.n_rows
     info = B.Info()
     if out is None:

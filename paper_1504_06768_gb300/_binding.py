@@ -33,7 +33,7 @@ class Options(C.Structure):
     _fields_ = [("method", C.c_int), ("precond", C.c_int), ("precision", C.c_int), ("tol", C.c_double),
                 ("maxiter", C.c_int), ("restart", C.c_int), ("drop_tol", C.c_double),
                 ("fill_factor", C.c_double), ("w", C.c_double), ("sigma", C.c_double),
-                ("use_rcm", C.c_int), ("seed", C.c_uint64)]
+                ("use_rcm", C.c_int), ("seed", C.c_uint64), ("inner_rtol", C.c_double)]
 
 
 class Info(C.Structure):
@@ -86,6 +86,7 @@ _SIGNATURES = {
                                        C.c_int, C.POINTER(Info)]),
     "ss_profile_enable": (C.c_int, [_P, C.c_int]),
     "ss_profile_read": (C.c_int, [_P, C.c_int, _I64P, _DP]),
+    "ss_launch_count": (C.c_ulonglong, []),
     "steady_state": (C.c_int, [_P, C.POINTER(CsrView), C.c_int, C.POINTER(CsrView), C.POINTER(Options),
                                _P, C.c_int, C.POINTER(Info)]),
 }

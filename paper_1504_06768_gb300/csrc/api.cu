@@ -140,6 +140,7 @@ extern "C" void ss_options_default(ss_options* o) {
     o->sigma = 1e-15;
     o->use_rcm = 1;
     o->seed = 0;
+    o->inner_rtol = 1e-5;
 }
 
 // ----------------------------------------------------------------- matrices
@@ -315,7 +316,7 @@ static ss_status ensure_f32(ss_ctx ctx, ss_mat A) {
     if (A->val32) return SS_OK;
     SS_TRY(dev_alloc_n(ctx, &A->val32, (size_t)A->m.nnz));
     if (A->m.nnz)
-        to_f32_vals<<<(unsigned)((A->m.nnz + 255) / 256), 256, 0, ctx->stream>>>(A->m.val, A->m.nnz, A->val32);
+        to_f32_vals<<<(ss_count_launch(), (unsigned)((A->m.nnz + 255) / 256)), 256, 0, ctx->stream>>>(A->m.val, A->m.nnz, A->val32);
     SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;
 }
@@ -534,7 +535,10 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
             double rn = 0.0;
             STEP(su_refine_residual(ctx, Ap->m, b, x, y, r64, b32, x32, scr, &rn));
             if (rn == 0.0) { status = SS_OK; lr = 0.0; break; }
-            STEP(bicgstab_dev32(ctx, Ap->m, Ap->val32, M, kw, b32, x32, 1e-4, opt.maxiter - total, &res));
+            // a stalled FP32 inner solve returns after a bounded number of iterations
+            const int cap = std::min(opt.maxiter - total, std::max(50, opt.maxiter / 5));
+            STEP(bicgstab_dev32(ctx, Ap->m, Ap->val32, M, kw, b32, x32, opt.inner_rtol > 0 ? opt.inner_rtol : 1e-5,
+                                cap, &res));
             total += res.iters;
             STEP(su_refine_update(ctx, n, x, scr, x32));
             if (res.status == SS_BREAKDOWN && res.iters == 0) { status = SS_BREAKDOWN; break; }

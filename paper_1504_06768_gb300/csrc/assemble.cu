@@ -297,14 +297,14 @@ ss_status transpose_csr(ss_ctx ctx, const DeviceCSR& a, DeviceCSR& t) {
     SS_TRY(dev_alloc_n(ctx, &t.col, (size_t)a.nnz));
     SS_TRY(dev_alloc_n(ctx, &t.val, (size_t)a.nnz));
     SS_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (a.n_cols + 1), ctx->stream));
-    if (a.nnz > 0) count_cols<<<grid_for(a.nnz, 256), 256, 0, ctx->stream>>>(a.col, a.nnz, cnt);
+    if (a.nnz > 0) count_cols<<<(ss_count_launch(), grid_for(a.nnz, 256)), 256, 0, ctx->stream>>>(a.col, a.nnz, cnt);
     SS_TRY(exclusive_scan_i32(ctx, cnt, t.row_ptr, a.n_cols, nullptr));
     SS_CUDA(ctx, cudaMemcpyAsync(cnt, t.row_ptr, sizeof(int32_t) * (a.n_cols + 1), cudaMemcpyDeviceToDevice,
                                  ctx->stream));
     if (a.n_rows > 0)
-        scatter_transpose<<<grid_for(a.n_rows, 128), 128, 0, ctx->stream>>>(CsrRef{a.row_ptr, a.col, a.val}, a.n_rows,
+        scatter_transpose<<<(ss_count_launch(), grid_for(a.n_rows, 128)), 128, 0, ctx->stream>>>(CsrRef{a.row_ptr, a.col, a.val}, a.n_rows,
                                                                             cnt, t.col, t.val);
-    if (t.n_rows > 0) sort_rows<<<grid_for(t.n_rows, 128), 128, 0, ctx->stream>>>(t.row_ptr, t.n_rows, t.col, t.val);
+    if (t.n_rows > 0) sort_rows<<<(ss_count_launch(), grid_for(t.n_rows, 128)), 128, 0, ctx->stream>>>(t.row_ptr, t.n_rows, t.col, t.val);
     SS_CUDA(ctx, cudaGetLastError());
     dev_free(ctx, cnt);
     return SS_OK;
@@ -320,13 +320,13 @@ ss_status ctc_csr(ss_ctx ctx, const DeviceCSR& c, const DeviceCSR& ct, DeviceCSR
     SS_TRY(dev_alloc_n(ctx, &cnt, (size_t)d + 1));
     SS_TRY(dev_alloc_n(ctx, &off, (size_t)d + 1));
     SS_TRY(dev_alloc_n(ctx, &cnt2, (size_t)d + 1));
-    ctc_count<<<grid_for(d, 128), 128, 0, ctx->stream>>>(CsrRef{ct.row_ptr, ct.col, ct.val},
+    ctc_count<<<(ss_count_launch(), grid_for(d, 128)), 128, 0, ctx->stream>>>(CsrRef{ct.row_ptr, ct.col, ct.val},
                                                           CsrRef{c.row_ptr, c.col, c.val}, d, cnt);
     int64_t total = 0;
     SS_TRY(exclusive_scan_i32(ctx, cnt, off, d, &total));
     SS_TRY(dev_alloc_n(ctx, &kcol, (size_t)total));
     SS_TRY(dev_alloc_n(ctx, &kval, (size_t)total));
-    ctc_fill<<<grid_for(d, 128), 128, 0, ctx->stream>>>(CsrRef{ct.row_ptr, ct.col, ct.val},
+    ctc_fill<<<(ss_count_launch(), grid_for(d, 128)), 128, 0, ctx->stream>>>(CsrRef{ct.row_ptr, ct.col, ct.val},
                                                          CsrRef{c.row_ptr, c.col, c.val}, d, off, kcol, kval, cnt2);
     SS_TRY(dev_alloc_n(ctx, &out.row_ptr, (size_t)d + 1));
     int64_t nnz = 0;
@@ -334,7 +334,7 @@ ss_status ctc_csr(ss_ctx ctx, const DeviceCSR& c, const DeviceCSR& ct, DeviceCSR
     out.nnz = nnz;
     SS_TRY(dev_alloc_n(ctx, &out.col, (size_t)nnz));
     SS_TRY(dev_alloc_n(ctx, &out.val, (size_t)nnz));
-    compact_rows<<<grid_for(d, 128), 128, 0, ctx->stream>>>(off, out.row_ptr, d, kcol, kval, out.col, out.val);
+    compact_rows<<<(ss_count_launch(), grid_for(d, 128)), 128, 0, ctx->stream>>>(off, out.row_ptr, d, kcol, kval, out.col, out.val);
     SS_CUDA(ctx, cudaGetLastError());
     dev_free(ctx, cnt);
     dev_free(ctx, off);
@@ -375,14 +375,14 @@ ss_status assemble_impl(ss_ctx ctx, const DeviceCSR& H, const std::vector<Device
     SS_TRY(dev_alloc_n(ctx, &off, (size_t)n + 1));
     SS_TRY(dev_alloc_n(ctx, &cnt2, (size_t)n + 1));
     CsrRef h{H.row_ptr, H.col, H.val}, ht{Ht.row_ptr, Ht.col, Ht.val};
-    lrow_count<<<grid_for(n, 256), 256, 0, ctx->stream>>>(h, ht, dops, n_c, d, cnt);
+    lrow_count<<<(ss_count_launch(), grid_for(n, 256)), 256, 0, ctx->stream>>>(h, ht, dops, n_c, d, cnt);
     int64_t total = 0;
     SS_TRY(exclusive_scan_i32(ctx, cnt, off, n, &total));
     unsigned long long* key = nullptr;
     double2* val = nullptr;
     SS_TRY(dev_alloc_n(ctx, &key, (size_t)total));
     SS_TRY(dev_alloc_n(ctx, &val, (size_t)total));
-    lrow_build<<<grid_for(n, 128), 128, 0, ctx->stream>>>(h, ht, dops, n_c, d, off, key, val, cnt2);
+    lrow_build<<<(ss_count_launch(), grid_for(n, 128)), 128, 0, ctx->stream>>>(h, ht, dops, n_c, d, off, key, val, cnt2);
     L.n_rows = L.n_cols = n;
     SS_TRY(dev_alloc_n(ctx, &L.row_ptr, (size_t)n + 1));
     int64_t nnz = 0;
@@ -390,7 +390,7 @@ ss_status assemble_impl(ss_ctx ctx, const DeviceCSR& H, const std::vector<Device
     L.nnz = nnz;
     SS_TRY(dev_alloc_n(ctx, &L.col, (size_t)nnz));
     SS_TRY(dev_alloc_n(ctx, &L.val, (size_t)nnz));
-    lrow_compact<<<grid_for(n, 256), 256, 0, ctx->stream>>>(off, L.row_ptr, n, key, val, L.col, L.val);
+    lrow_compact<<<(ss_count_launch(), grid_for(n, 256)), 256, 0, ctx->stream>>>(off, L.row_ptr, n, key, val, L.col, L.val);
     SS_CUDA(ctx, cudaGetLastError());
 
     dev_free(ctx, key);

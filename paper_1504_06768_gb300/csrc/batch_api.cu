@@ -268,7 +268,7 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
     bp.tol = opt.tol;
     bp.maxiter = opt.maxiter;
     bp.mixed = mixed ? 1 : 0;
-    bp.inner_rtol = 1e-4;
+    bp.inner_rtol = opt.inner_rtol > 0 ? opt.inner_rtol : 1e-5;
     bp.power = 0;
     bp.seed = opt.seed;
     BSTEP(batch_launch(ctx, dsys, (int)hs.size(), bp, max_n, ctl, ctl + 1));

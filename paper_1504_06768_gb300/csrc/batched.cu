@@ -24,7 +24,7 @@ namespace {
 constexpr int BT = BATCH_THREADS;
 constexpr int NW = BT / 32;
 constexpr unsigned FULLM = 0xffffffffu;
-constexpr long long SPIN_LIMIT = 1ll << 24;
+constexpr long long SPIN_LIMIT = 1ll << 22;   // with back-off: a wait gives up after ~0.3 s
 
 // ------------------------------------------------------------ arithmetic
 __device__ __forceinline__ double2 D(double2 a) { return a; }
@@ -81,12 +81,28 @@ __device__ __forceinline__ bool negligible(double2 a, double nu, double nv) {
 }
 
 // ------------------------------------------------------ triangular solves
+// Waits (bounded) until fl[j] == epoch.  Idle warps sleep between polls so
+// that the warps doing the work keep the issue slots and the shared-memory
+// pipe.
+__device__ __forceinline__ bool wait_flag(volatile uint32_t* fl, int32_t j, uint32_t epoch) {
+    if (fl[j] == epoch) return true;
+    long long spins = 0;
+    unsigned ns = 8;
+    while (fl[j] != epoch) {
+        __nanosleep(ns);
+        if (ns < 64) ns <<= 1;
+        if (++spins > SPIN_LIMIT) return false;
+    }
+    return true;
+}
+
 template <bool LOWER, int G, class T>
 __device__ void cta_trsv_g(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, const T* __restrict__ val,
                            const int32_t* __restrict__ dpos, const T* __restrict__ inv,
                            const int32_t* __restrict__ units, int32_t nunits, T* buf, volatile uint32_t* fl,
                            uint32_t epoch, int* err) {
     constexpr int R = 32 / G;
+    constexpr int MAXE = 4;            // entries per lane held in registers before waiting
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane / G, sub = lane % G;
     for (int32_t u = warp; u < nunits; u += NW) {
         const int32_t i = units[u * R + grp];
@@ -95,17 +111,30 @@ __device__ void cta_trsv_g(const int32_t* __restrict__ rp, const int32_t* __rest
             if (LOWER) { s = rp[i]; e = dpos[i]; }
             else { s = dpos[i] + 1; e = rp[i + 1]; }
         }
-        bool bad = false;
-        for (int32_t k = s + sub; k < e; k += G) {
-            const int32_t j = col[k];
-            long long spins = 0;
-            while (fl[j] != epoch) {
-                if (++spins > SPIN_LIMIT) { bad = true; break; }
-            }
+        int32_t jj[MAXE];
+        T vv[MAXE];
+#pragma unroll
+        for (int q = 0; q < MAXE; ++q) {
+            const int32_t k = s + sub + q * G;
+            const bool ok = k < e;
+            jj[q] = ok ? col[k] : -1;
+            vv[q] = ok ? val[k] : zero<T>();
         }
+        bool bad = false;
+#pragma unroll
+        for (int q = 0; q < MAXE; ++q)
+            if (jj[q] >= 0 && !wait_flag(fl, jj[q], epoch)) bad = true;
         __threadfence_block();
         T acc = zero<T>();
-        for (int32_t k = s + sub; k < e; k += G) acc = fmac(val[k], buf[col[k]], acc);
+#pragma unroll
+        for (int q = 0; q < MAXE; ++q)
+            if (jj[q] >= 0) acc = fmac(vv[q], buf[jj[q]], acc);
+        for (int32_t k = s + sub + MAXE * G; k < e; k += G) {      // long rows
+            const int32_t j = col[k];
+            if (!wait_flag(fl, j, epoch)) bad = true;
+            __threadfence_block();
+            acc = fmac(val[k], buf[j], acc);
+        }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
             T other = shd(acc, o);
@@ -507,7 +536,10 @@ __device__ void solve_mixed(BatchSys& S, const BatchParams& P, unsigned char* sm
             x32[i] = make_float2(0.f, 0.f);
         }
         __syncthreads();
-        KResult kr = cta_bicgstab<float2>(c, x32, b32, wk, P.inner_rtol, P.maxiter - total);
+        // an FP32 inner solve that stalls above its tolerance returns after a bounded
+        // number of iterations so that the FP64 refinement can continue
+        const int cap = min(P.maxiter - total, max(50, P.maxiter / 5));
+        KResult kr = cta_bicgstab<float2>(c, x32, b32, wk, P.inner_rtol, cap);
         total += kr.iters;
         for (int32_t i = threadIdx.x; i < n; i += BT) {
             x[i].x += rn * (double)x32[i].x;
@@ -576,7 +608,10 @@ ss_status batch_launch(ss_ctx ctx, BatchSys* dsys, int nsys, const BatchParams& 
     const size_t smem = batch_smem_bytes(max_n, p.mixed != 0);
     SS_CUDA(ctx, cudaFuncSetAttribute(batched_solver, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = std::max(1, std::min(nsys, ctx->num_sms > 0 ? ctx->num_sms : 1));
-    batched_solver<<<grid, BT, smem, ctx->stream>>>(dsys, nsys, p, queue, err);
+    {
+        ProfScope ps(ctx, PROF_BATCHED);
+        batched_solver<<<(ss_count_launch(), grid), BT, smem, ctx->stream>>>(dsys, nsys, p, queue, err);
+    }
     SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;
 }

@@ -53,7 +53,7 @@ struct DeviceCSR {          // complex FP64 CSR on the device
 };
 
 // Kernel classes timed by the optional per-launch profiler.
-enum ProfKind { PROF_SPMV = 0, PROF_TRSV_LOWER = 1, PROF_TRSV_UPPER = 2, PROF_NKINDS = 3 };
+enum ProfKind { PROF_SPMV = 0, PROF_TRSV_LOWER = 1, PROF_TRSV_UPPER = 2, PROF_BATCHED = 3, PROF_NKINDS = 4 };
 
 struct ProfRec {
     cudaEvent_t a, b;
@@ -119,6 +119,10 @@ ss_status cuda_check(ss_ctx ctx, cudaError_t e, const char* what);
         ss_status _s = (call);                                          \
         if (_s != SS_OK) return _s;                                     \
     } while (0)
+
+// Every kernel launch of the library goes through ss_count_launch() (in the
+// grid expression of the launch), so the total is available to callers.
+int ss_count_launch();
 
 // RAII event pair around one launch when the context's profiler is on.
 struct ProfScope {

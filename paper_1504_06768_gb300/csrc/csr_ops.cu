@@ -194,8 +194,8 @@ ss_status mean_abs_diag(ss_ctx ctx, const DeviceCSR& L, double* w) {
     const int nb = 256;
     double* part = nullptr;
     SS_TRY(dev_alloc_n(ctx, &part, nb + 1));
-    abs_diag_partial<<<nb, 256, 0, ctx->stream>>>(L.row_ptr, L.col, L.val, L.n_rows, part);
-    sum_partials<<<1, 256, 0, ctx->stream>>>(part, nb, 1.0 / (double)L.n_rows, part + nb);
+    abs_diag_partial<<<(ss_count_launch(), nb), 256, 0, ctx->stream>>>(L.row_ptr, L.col, L.val, L.n_rows, part);
+    sum_partials<<<(ss_count_launch(), 1), 256, 0, ctx->stream>>>(part, nb, 1.0 / (double)L.n_rows, part + nb);
     SS_CUDA(ctx, cudaMemcpyAsync(w, part + nb, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     dev_free(ctx, part);
@@ -214,7 +214,7 @@ ss_status add_trace_row_impl(ss_ctx ctx, const DeviceCSR& L, int64_t d, double w
     SS_TRY(dev_alloc_n(ctx, &tcol, (size_t)cap));
     SS_TRY(dev_alloc_n(ctx, &tval, (size_t)cap));
     SS_TRY(dev_alloc_n(ctx, &tlen, 1));
-    trace_row0<<<1, 32, 0, ctx->stream>>>(L.row_ptr, L.col, L.val, d, w, tcol, tval, tlen);
+    trace_row0<<<(ss_count_launch(), 1), 32, 0, ctx->stream>>>(L.row_ptr, L.col, L.val, d, w, tcol, tval, tlen);
     int32_t len0 = 0;
     SS_CUDA(ctx, cudaMemcpyAsync(&len0, tlen, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
     SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -224,10 +224,10 @@ ss_status add_trace_row_impl(ss_ctx ctx, const DeviceCSR& L, int64_t d, double w
     SS_TRY(dev_alloc_n(ctx, &out.row_ptr, (size_t)n + 1));
     SS_TRY(dev_alloc_n(ctx, &out.col, (size_t)out.nnz));
     SS_TRY(dev_alloc_n(ctx, &out.val, (size_t)out.nnz));
-    shift_rows<<<grid_for(n + 1, 256), 256, 0, ctx->stream>>>(L.row_ptr, n, tlen, out.row_ptr);
+    shift_rows<<<(ss_count_launch(), grid_for(n + 1, 256)), 256, 0, ctx->stream>>>(L.row_ptr, n, tlen, out.row_ptr);
     int64_t tail = L.nnz - h_rp[1];
     if (tail > 0)
-        copy_tail<<<grid_for(tail, 256), 256, 0, ctx->stream>>>(L.row_ptr, L.col, L.val, L.nnz, out.row_ptr,
+        copy_tail<<<(ss_count_launch(), grid_for(tail, 256)), 256, 0, ctx->stream>>>(L.row_ptr, L.col, L.val, L.nnz, out.row_ptr,
                                                                 out.col, out.val);
     SS_CUDA(ctx, cudaMemcpyAsync(out.col, tcol, sizeof(int32_t) * len0, cudaMemcpyDeviceToDevice, ctx->stream));
     SS_CUDA(ctx, cudaMemcpyAsync(out.val, tval, sizeof(double2) * len0, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -245,7 +245,7 @@ ss_status add_shift_impl(ss_ctx ctx, const DeviceCSR& L, double sigma, DeviceCSR
     SS_TRY(dev_alloc_n(ctx, &dpos, (size_t)n));
     SS_TRY(dev_alloc_n(ctx, &cnt, (size_t)n + 1));
     SS_TRY(find_diag(ctx, L, dpos));
-    shift_count<<<grid_for(n, 256), 256, 0, ctx->stream>>>(L.row_ptr, dpos, n, cnt);
+    shift_count<<<(ss_count_launch(), grid_for(n, 256)), 256, 0, ctx->stream>>>(L.row_ptr, dpos, n, cnt);
     out.n_rows = out.n_cols = n;
     SS_TRY(dev_alloc_n(ctx, &out.row_ptr, (size_t)n + 1));
     int64_t nnz = 0;
@@ -253,7 +253,7 @@ ss_status add_shift_impl(ss_ctx ctx, const DeviceCSR& L, double sigma, DeviceCSR
     out.nnz = nnz;
     SS_TRY(dev_alloc_n(ctx, &out.col, (size_t)nnz));
     SS_TRY(dev_alloc_n(ctx, &out.val, (size_t)nnz));
-    shift_fill<<<grid_for(n, 256), 256, 0, ctx->stream>>>(L.row_ptr, L.col, L.val, n, sigma, out.row_ptr, out.col,
+    shift_fill<<<(ss_count_launch(), grid_for(n, 256)), 256, 0, ctx->stream>>>(L.row_ptr, L.col, L.val, n, sigma, out.row_ptr, out.col,
                                                           out.val);
     SS_CUDA(ctx, cudaGetLastError());
     dev_free(ctx, dpos);
@@ -269,15 +269,15 @@ ss_status permute_impl(ss_ctx ctx, const DeviceCSR& A, const int32_t* perm_host,
     SS_TRY(dev_alloc_n(ctx, &iperm, (size_t)n));
     SS_TRY(dev_alloc_n(ctx, &cnt, (size_t)n + 1));
     SS_CUDA(ctx, cudaMemcpyAsync(perm, perm_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
-    invert_perm<<<grid_for(n, 256), 256, 0, ctx->stream>>>(perm, n, iperm);
-    perm_count<<<grid_for(n, 256), 256, 0, ctx->stream>>>(A.row_ptr, perm, n, cnt);
+    invert_perm<<<(ss_count_launch(), grid_for(n, 256)), 256, 0, ctx->stream>>>(perm, n, iperm);
+    perm_count<<<(ss_count_launch(), grid_for(n, 256)), 256, 0, ctx->stream>>>(A.row_ptr, perm, n, cnt);
     out.n_rows = out.n_cols = n;
     out.nnz = A.nnz;
     SS_TRY(dev_alloc_n(ctx, &out.row_ptr, (size_t)n + 1));
     SS_TRY(exclusive_scan_i32(ctx, cnt, out.row_ptr, n, nullptr));
     SS_TRY(dev_alloc_n(ctx, &out.col, (size_t)A.nnz));
     SS_TRY(dev_alloc_n(ctx, &out.val, (size_t)A.nnz));
-    perm_fill<<<grid_for(n, 128), 128, 0, ctx->stream>>>(A.row_ptr, A.col, A.val, perm, iperm, n, out.row_ptr,
+    perm_fill<<<(ss_count_launch(), grid_for(n, 128)), 128, 0, ctx->stream>>>(A.row_ptr, A.col, A.val, perm, iperm, n, out.row_ptr,
                                                          out.col, out.val);
     SS_CUDA(ctx, cudaGetLastError());
     dev_free(ctx, perm);
@@ -294,8 +294,8 @@ ss_status bandwidth_profile_impl(ss_ctx ctx, const DeviceCSR& A, int64_t* bw, in
     SS_TRY(dev_alloc_n(ctx, &colmax, (size_t)n));
     SS_CUDA(ctx, cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 4, ctx->stream));
     SS_CUDA(ctx, cudaMemsetAsync(colmax, 0, sizeof(int32_t) * n, ctx->stream));
-    bw_rows<<<grid_for(n, 256), 256, 0, ctx->stream>>>(A.row_ptr, A.col, n, acc, colmax);
-    sum_colmax<<<grid_for(n, 256), 256, 0, ctx->stream>>>(colmax, n, acc);
+    bw_rows<<<(ss_count_launch(), grid_for(n, 256)), 256, 0, ctx->stream>>>(A.row_ptr, A.col, n, acc, colmax);
+    sum_colmax<<<(ss_count_launch(), grid_for(n, 256)), 256, 0, ctx->stream>>>(colmax, n, acc);
     unsigned long long h[4];
     SS_CUDA(ctx, cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

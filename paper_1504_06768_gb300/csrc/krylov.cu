@@ -490,20 +490,20 @@ static ss_status bicgstab_any(ss_ctx ctx, const DeviceCSR& A, const float2* val3
     int* halt = &w.st->halt;
     SS_TRY(set_params(ctx, w, tol, maxiter, 0));
     spmv_any<T>(ctx, A, val32, x, v, nullptr);
-    bicg_init<T><<<nb, RED_THREADS, 0, ctx->stream>>>(n, b, v, r, rhat, w.st);
+    bicg_init<T><<<(ss_count_launch(), nb), RED_THREADS, 0, ctx->stream>>>(n, b, v, r, rhat, w.st);
     SS_CUDA(ctx, cudaGetLastError());
     int queued = 0, chunk = 2;
     while (true) {
         for (int c = 0; c < chunk; ++c) {
-            bicg_p<T><<<eg, RED_THREADS, 0, ctx->stream>>>(n, r, v, p, w.st);
+            bicg_p<T><<<(ss_count_launch(), eg), RED_THREADS, 0, ctx->stream>>>(n, r, v, p, w.st);
             SS_TRY(prec_any(ctx, M, p, phat, halt));
             spmv_any<T>(ctx, A, val32, phat, v, halt);
-            bicg_rv<T><<<nb, RED_THREADS, 0, ctx->stream>>>(n, rhat, v, w.st);
-            bicg_s<T><<<nb, RED_THREADS, 0, ctx->stream>>>(n, r, v, s, w.st);
+            bicg_rv<T><<<(ss_count_launch(), nb), RED_THREADS, 0, ctx->stream>>>(n, rhat, v, w.st);
+            bicg_s<T><<<(ss_count_launch(), nb), RED_THREADS, 0, ctx->stream>>>(n, r, v, s, w.st);
             SS_TRY(prec_any(ctx, M, s, shat, halt));
             spmv_any<T>(ctx, A, val32, shat, t, halt);
-            bicg_ts<T><<<nb, RED_THREADS, 0, ctx->stream>>>(n, t, s, w.st);
-            bicg_xr<T><<<nb, RED_THREADS, 0, ctx->stream>>>(n, x, phat, shat, s, t, r, rhat, w.st);
+            bicg_ts<T><<<(ss_count_launch(), nb), RED_THREADS, 0, ctx->stream>>>(n, t, s, w.st);
+            bicg_xr<T><<<(ss_count_launch(), nb), RED_THREADS, 0, ctx->stream>>>(n, x, phat, shat, s, t, r, rhat, w.st);
         }
         SS_CUDA(ctx, cudaGetLastError());
         queued += chunk;
@@ -546,8 +546,8 @@ ss_status gmres_dev(ss_ctx ctx, const DeviceCSR& A, ss_prec M, KrylovWork& w, co
     while (true) {
         // restart: y = A x into V_1 as scratch, r into V_m, v_0 = r / beta
         { ProfScope ps_(ctx, PROF_SPMV); spmv_launch(A, x, V + n, nullptr, ctx->stream); }
-        gm_restart<<<nb, RED_THREADS, 0, ctx->stream>>>(n, b, V + n, rv, w.st);
-        gm_scale<<<eg, RED_THREADS, 0, ctx->stream>>>(n, rv, V, w.st);
+        gm_restart<<<(ss_count_launch(), nb), RED_THREADS, 0, ctx->stream>>>(n, b, V + n, rv, w.st);
+        gm_scale<<<(ss_count_launch(), eg), RED_THREADS, 0, ctx->stream>>>(n, rv, V, w.st);
         for (int j = 0; j < m; ++j) {
             double2* vj = V + (size_t)j * n;
             double2* zj = Z + (size_t)j * n;
@@ -556,13 +556,13 @@ ss_status gmres_dev(ss_ctx ctx, const DeviceCSR& A, ss_prec M, KrylovWork& w, co
             { ProfScope ps_(ctx, PROF_SPMV); spmv_launch(A, zj, wv, halt, ctx->stream); }
             for (int pass = 0; pass < 2; ++pass) {      // classical Gram-Schmidt, twice
                 for (int base = 0; base <= j; base += 8)
-                    gm_dots<8><<<nb, RED_THREADS, 0, ctx->stream>>>(n, V, n, j, base, wv, w.st, pass);
-                gm_orth_update<<<eg, RED_THREADS, 0, ctx->stream>>>(n, V, n, j, wv, w.st);
+                    gm_dots<8><<<(ss_count_launch(), nb), RED_THREADS, 0, ctx->stream>>>(n, V, n, j, base, wv, w.st, pass);
+                gm_orth_update<<<(ss_count_launch(), eg), RED_THREADS, 0, ctx->stream>>>(n, V, n, j, wv, w.st);
             }
-            gm_norm<<<nb, RED_THREADS, 0, ctx->stream>>>(n, wv, j, w.st);
-            gm_scale<<<eg, RED_THREADS, 0, ctx->stream>>>(n, wv, wv, w.st);
+            gm_norm<<<(ss_count_launch(), nb), RED_THREADS, 0, ctx->stream>>>(n, wv, j, w.st);
+            gm_scale<<<(ss_count_launch(), eg), RED_THREADS, 0, ctx->stream>>>(n, wv, wv, w.st);
         }
-        gm_update_x<<<eg, RED_THREADS, 0, ctx->stream>>>(n, Z, n, x, w.st);
+        gm_update_x<<<(ss_count_launch(), eg), RED_THREADS, 0, ctx->stream>>>(n, Z, n, x, w.st);
         SS_CUDA(ctx, cudaGetLastError());
         SS_TRY(read_state(ctx, w));
         if (w.host_st->done) break;

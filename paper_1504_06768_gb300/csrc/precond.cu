@@ -258,7 +258,7 @@ static ss_status analyse(ss_ctx ctx, ss_prec M, const std::vector<int32_t>& hrp,
     SS_TRY(dev_alloc_n(ctx, &M->tickets, 2));
     SS_TRY(dev_alloc_n(ctx, &M->err, 1));
     SS_TRY(dev_alloc_n(ctx, &M->tmp, (size_t)n));
-    fill_pending<double2><<<256, 256, 0, ctx->stream>>>(n, M->tmp);
+    fill_pending<double2><<<(ss_count_launch(), 256), 256, 0, ctx->stream>>>(n, M->tmp);
     SS_CUDA(ctx, cudaMemsetAsync(M->tickets, 0, sizeof(unsigned long long) * 2, ctx->stream));
     SS_CUDA(ctx, cudaMemsetAsync(M->err, 0, sizeof(int), ctx->stream));
     return SS_OK;
@@ -282,14 +282,14 @@ ss_status ilu0_device(ss_ctx ctx, const DeviceCSR& A, ss_prec M) {
     SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     std::vector<int32_t> lorder, lptr;
     SS_TRY(analyse(ctx, M, hrp, hcol, lorder, lptr));
-    check_missing_diag<<<grid_for(n, 256), 256, 0, ctx->stream>>>(M->diag_pos, n, M->err);
+    check_missing_diag<<<(ss_count_launch(), grid_for(n, 256)), 256, 0, ctx->stream>>>(M->diag_pos, n, M->err);
     int herr = 0;
     SS_CUDA(ctx, cudaMemcpyAsync(&herr, M->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (herr) return set_error(ctx, SS_ZERO_PIVOT, "iLU(0): missing diagonal entry");
     for (int32_t l = 0; l < M->lower.n_levels; ++l) {
         int32_t rows = lptr[l + 1] - lptr[l];
-        ilu0_level<<<grid_for((int64_t)rows * 32, 256), 256, 0, ctx->stream>>>(
+        ilu0_level<<<(ss_count_launch(), grid_for((int64_t)rows * 32, 256)), 256, 0, ctx->stream>>>(
             M->f.row_ptr, M->f.col, M->f.val, M->diag_pos, M->lower.order, lptr[l], lptr[l + 1], M->err);
     }
     SS_CUDA(ctx, cudaGetLastError());
@@ -321,12 +321,12 @@ ss_status prec_finish(ss_ctx ctx, ss_prec M, bool want_fp32) {
         SS_TRY(dev_alloc_n(ctx, &M->val32, (size_t)M->f.nnz));
         SS_TRY(dev_alloc_n(ctx, &M->inv_diag32, (size_t)n));
         SS_TRY(dev_alloc_n(ctx, &M->tmp32, (size_t)n));
-        fill_pending<float2><<<256, 256, 0, ctx->stream>>>(n, M->tmp32);
+        fill_pending<float2><<<(ss_count_launch(), 256), 256, 0, ctx->stream>>>(n, M->tmp32);
     }
-    make_inv_diag<<<grid_for(n, 256), 256, 0, ctx->stream>>>(M->f.val, M->diag_pos, n, M->inv_diag, M->inv_diag32,
+    make_inv_diag<<<(ss_count_launch(), grid_for(n, 256)), 256, 0, ctx->stream>>>(M->f.val, M->diag_pos, n, M->inv_diag, M->inv_diag32,
                                                              M->err);
     if (want_fp32 && M->f.nnz > 0)
-        to_f32<<<grid_for(M->f.nnz, 256), 256, 0, ctx->stream>>>(M->f.val, M->f.nnz, M->val32);
+        to_f32<<<(ss_count_launch(), grid_for(M->f.nnz, 256)), 256, 0, ctx->stream>>>(M->f.val, M->f.nnz, M->val32);
     SS_CUDA(ctx, cudaGetLastError());
     int herr = 0;
     SS_CUDA(ctx, cudaMemcpyAsync(&herr, M->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -343,7 +343,7 @@ static void launch_trsv(ss_ctx ctx, ss_prec M, const TriLevels& L, const T* vals
     const unsigned g = (unsigned)((L.n_units * 32 + threads - 1) / threads);
 #define SS_TRSV_CASE(GG)                                                                                    \
     case GG:                                                                                                \
-        sptrsv_syncfree<LOWER, GG, T><<<g, threads, 0, ctx->stream>>>(M->f.row_ptr, M->f.col, vals,        \
+        sptrsv_syncfree<LOWER, GG, T><<<(ss_count_launch(), g), threads, 0, ctx->stream>>>(M->f.row_ptr, M->f.col, vals,        \
                                                                        M->diag_pos, inv, L.units, L.n_units, \
                                                                        b, x, other, ticket, M->err, halt);   \
         break;

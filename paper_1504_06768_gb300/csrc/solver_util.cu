@@ -188,45 +188,45 @@ __global__ void axpy_from32(int64_t n, double2* __restrict__ x, const double* __
 ss_status su_refine_residual(ss_ctx ctx, const DeviceCSR& A, const double2* b, const double2* x, double2* y,
                              double2* r, float2* b32, float2* x32, double* scratch, double* rnorm) {
     { ProfScope ps_(ctx, PROF_SPMV); spmv_launch(A, x, y, nullptr, ctx->stream); }
-    resid_partial<<<NB, 256, 0, ctx->stream>>>(A.n_rows, b, y, r, scratch);
-    sum_part<<<1, 256, 0, ctx->stream>>>(scratch, NB, scratch + NB);
+    resid_partial<<<(ss_count_launch(), NB), 256, 0, ctx->stream>>>(A.n_rows, b, y, r, scratch);
+    sum_part<<<(ss_count_launch(), 1), 256, 0, ctx->stream>>>(scratch, NB, scratch + NB);
     double h = 0.0;
     SS_CUDA(ctx, cudaMemcpyAsync(&h, scratch + NB, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     *rnorm = sqrt(h);
-    if (h > 0.0) scale_to32<<<1024, 256, 0, ctx->stream>>>(A.n_rows, r, scratch + NB, b32, x32);
+    if (h > 0.0) scale_to32<<<(ss_count_launch(), 1024), 256, 0, ctx->stream>>>(A.n_rows, r, scratch + NB, b32, x32);
     SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;
 }
 
 ss_status su_refine_update(ss_ctx ctx, int64_t n, double2* x, const double* scratch, const float2* c) {
-    axpy_from32<<<1024, 256, 0, ctx->stream>>>(n, x, scratch + NB, c);
+    axpy_from32<<<(ss_count_launch(), 1024), 256, 0, ctx->stream>>>(n, x, scratch + NB, c);
     SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;
 }
 
 ss_status su_zero(ss_ctx ctx, int64_t n, double2* v) {
-    fill_zero<<<grid_for(n, 256) > 1024 ? 1024 : grid_for(n, 256), 256, 0, ctx->stream>>>(n, v);
+    fill_zero<<<(ss_count_launch(), grid_for(n, 256) > 1024 ? 1024 : grid_for(n, 256)), 256, 0, ctx->stream>>>(n, v);
     SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;
 }
 
 ss_status su_start_vector(ss_ctx ctx, int64_t n, uint64_t seed, const int32_t* perm_dev, double2* x) {
-    start_vec<<<1024, 256, 0, ctx->stream>>>(n, seed, perm_dev, x);
+    start_vec<<<(ss_count_launch(), 1024), 256, 0, ctx->stream>>>(n, seed, perm_dev, x);
     SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;
 }
 
 ss_status su_normalise(ss_ctx ctx, int64_t n, double2* x, double* scratch /* NB + 1 */) {
-    norm2_partial<<<NB, 256, 0, ctx->stream>>>(n, x, scratch);
-    sum_part<<<1, 256, 0, ctx->stream>>>(scratch, NB, scratch + NB);
-    scale_by<<<1024, 256, 0, ctx->stream>>>(n, x, scratch + NB);
+    norm2_partial<<<(ss_count_launch(), NB), 256, 0, ctx->stream>>>(n, x, scratch);
+    sum_part<<<(ss_count_launch(), 1), 256, 0, ctx->stream>>>(scratch, NB, scratch + NB);
+    scale_by<<<(ss_count_launch(), 1024), 256, 0, ctx->stream>>>(n, x, scratch + NB);
     SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;
 }
 
 ss_status su_trace(ss_ctx ctx, int64_t d, const int32_t* tidx, const double2* x, double2* out) {
-    trace_kernel<<<1, 256, 0, ctx->stream>>>(d, tidx, x, out);
+    trace_kernel<<<(ss_count_launch(), 1), 256, 0, ctx->stream>>>(d, tidx, x, out);
     SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;
 }
@@ -237,9 +237,9 @@ ss_status su_lrho(ss_ctx ctx, const DeviceCSR& A, const double2* x, int mode, do
                   int64_t d, const int32_t* tidx, double2* y, double* scratch /* NB + 1 */, double2* trace_dev,
                   double* out, double2* trace_host) {
     { ProfScope ps_(ctx, PROF_SPMV); spmv_launch(A, x, y, nullptr, ctx->stream); }
-    trace_kernel<<<1, 256, 0, ctx->stream>>>(d, tidx, x, trace_dev);
-    lrho_partial<<<NB, 256, 0, ctx->stream>>>(A.n_rows, y, x, mode, w_or_sigma, r0, trace_dev, scratch);
-    sum_part<<<1, 256, 0, ctx->stream>>>(scratch, NB, scratch + NB);
+    trace_kernel<<<(ss_count_launch(), 1), 256, 0, ctx->stream>>>(d, tidx, x, trace_dev);
+    lrho_partial<<<(ss_count_launch(), NB), 256, 0, ctx->stream>>>(A.n_rows, y, x, mode, w_or_sigma, r0, trace_dev, scratch);
+    sum_part<<<(ss_count_launch(), 1), 256, 0, ctx->stream>>>(scratch, NB, scratch + NB);
     double h = 0.0;
     double2 tr;
     SS_CUDA(ctx, cudaMemcpyAsync(&h, scratch + NB, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -253,16 +253,16 @@ ss_status su_lrho(ss_ctx ctx, const DeviceCSR& A, const double2* x, int mode, do
 
 ss_status su_finalise(ss_ctx ctx, int64_t n, const int32_t* perm_dev, const double2* x, const double2* trace_dev,
                       double2* rho_dev) {
-    unpermute_normalise<<<1024, 256, 0, ctx->stream>>>(n, perm_dev, x, trace_dev, rho_dev);
+    unpermute_normalise<<<(ss_count_launch(), 1024), 256, 0, ctx->stream>>>(n, perm_dev, x, trace_dev, rho_dev);
     SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;
 }
 
 ss_status su_condest(ss_ctx ctx, ss_prec M, int64_t n, double2* ones, double2* z, double* scratch, double* out) {
-    fill_ones<<<1024, 256, 0, ctx->stream>>>(n, ones);
+    fill_ones<<<(ss_count_launch(), 1024), 256, 0, ctx->stream>>>(n, ones);
     SS_TRY(prec_apply_dev(ctx, M, ones, z));
-    max_abs_partial<<<NB, 256, 0, ctx->stream>>>(n, z, scratch);
-    max_part<<<1, 1, 0, ctx->stream>>>(scratch, NB, scratch + NB);
+    max_abs_partial<<<(ss_count_launch(), NB), 256, 0, ctx->stream>>>(n, z, scratch);
+    max_part<<<(ss_count_launch(), 1), 1, 0, ctx->stream>>>(scratch, NB, scratch + NB);
     SS_CUDA(ctx, cudaMemcpyAsync(out, scratch + NB, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     SS_TRY(prec_check_error(ctx, M));

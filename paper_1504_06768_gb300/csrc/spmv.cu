@@ -20,7 +20,7 @@ int spmv_group_size(int64_t n_rows, int64_t nnz) {
 template <int G>
 static void launch_f64(const DeviceCSR& A, const double2* x, double2* y, const int* halt, cudaStream_t s) {
     const int threads = 256;
-    spmv_kernel<G, double2, double2><<<grid_for(A.n_rows * G, threads), threads, 0, s>>>(
+    spmv_kernel<G, double2, double2><<<(ss_count_launch(), grid_for(A.n_rows * G, threads)), threads, 0, s>>>(
         A.row_ptr, A.col, A.val, A.n_rows, x, y, halt);
 }
 
@@ -28,7 +28,7 @@ template <int G>
 static void launch_f32(const DeviceCSR& A, const float2* val32, const float2* x, float2* y, const int* halt,
                        cudaStream_t s) {
     const int threads = 256;
-    spmv_kernel<G, float2, float2><<<grid_for(A.n_rows * G, threads), threads, 0, s>>>(
+    spmv_kernel<G, float2, float2><<<(ss_count_launch(), grid_for(A.n_rows * G, threads)), threads, 0, s>>>(
         A.row_ptr, A.col, val32, A.n_rows, x, y, halt);
 }
 

@@ -1,4 +1,5 @@
 // Errors, device allocation, scans and small CSR helpers.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 
@@ -111,9 +112,9 @@ ss_status exclusive_scan_i32(ss_ctx ctx, const int32_t* counts, int32_t* out, in
     long long* sums = nullptr;
     SS_TRY(dev_alloc_n(ctx, &sums, (size_t)nb + 1));
     long long* tot = sums + nb;
-    scan_block_sums<<<(unsigned)nb, SCAN_BLOCK, 0, ctx->stream>>>(counts, n, sums);
-    scan_sums_single<<<1, SCAN_BLOCK, 0, ctx->stream>>>(sums, nb, tot);
-    scan_apply<<<(unsigned)nb, SCAN_BLOCK, 0, ctx->stream>>>(counts, n, sums, out, tot);
+    scan_block_sums<<<(ss_count_launch(), (unsigned)nb), SCAN_BLOCK, 0, ctx->stream>>>(counts, n, sums);
+    scan_sums_single<<<(ss_count_launch(), 1), SCAN_BLOCK, 0, ctx->stream>>>(sums, nb, tot);
+    scan_apply<<<(ss_count_launch(), (unsigned)nb), SCAN_BLOCK, 0, ctx->stream>>>(counts, n, sums, out, tot);
     SS_CUDA(ctx, cudaGetLastError());
     if (!total) {              // the caller knows the total fits: stay asynchronous
         dev_free(ctx, sums);
@@ -145,7 +146,7 @@ __global__ void find_diag_kernel(const int32_t* __restrict__ rp, const int32_t* 
 ss_status find_diag(ss_ctx ctx, const DeviceCSR& m, int32_t* diag_pos) {
     if (m.n_rows == 0) return SS_OK;
     unsigned g = (unsigned)((m.n_rows + 255) / 256);
-    find_diag_kernel<<<g, 256, 0, ctx->stream>>>(m.row_ptr, m.col, m.n_rows, diag_pos);
+    find_diag_kernel<<<(ss_count_launch(), g), 256, 0, ctx->stream>>>(m.row_ptr, m.col, m.n_rows, diag_pos);
     SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;
 }
@@ -253,3 +254,14 @@ extern "C" ss_status ss_profile_read(ss_ctx ctx, int kind, int64_t* launches, do
     if (total_ms) *total_ms = ms;
     return SS_OK;
 }
+
+// ------------------------------------------------------------ launch count
+
+static std::atomic<unsigned long long> g_launches{0};
+
+int ss_count_launch() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return 0;
+}
+
+extern "C" unsigned long long ss_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }

@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "lindblad_ss.h")
 def _declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w]*\s*\*?\s+\*?([A-Za-z_]\w*)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?(?:[A-Za-z_]\w*[\s\*]+)+([A-Za-z_]\w*)\s*\(", src, flags=re.M)
     return sorted(set(n for n in names if n not in ("if", "while", "return")))
 
 
