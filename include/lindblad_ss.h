@@ -214,6 +214,29 @@ void ss_prec_free(ss_prec M);
 ss_status krylov_solve(ss_ctx ctx, ss_mat A, ss_prec M, int krylov, const double* b, double* x,
                        double tol, int maxiter, int restart, int* iters_out, double* resid_out);
 
+/* Largest system krylov_solve_noalloc accepts (complex unknowns). */
+#define SS_NOALLOC_MAX_N 65536
+
+/* krylov_solve with SS_KRYLOV_BICGSTAB (same iteration, same stop and
+ * breakdown rules, same results) for callers that cannot allocate memory
+ * during the call: a real-time or control loop with a fixed memory budget, or
+ * a host that routes every device allocation through its own pool.  This
+ * call makes no cudaMalloc/cudaFree or other allocation: its workspace (eight
+ * Krylov vectors of up to SS_NOALLOC_MAX_N = 65,536 complex doubles, the
+ * solver state and the reduction partials, about 8.3 MiB) is a fixed array in
+ * the library's device memory that every GPU loading the library holds until
+ * the process exits.  The array's device address is looked up once per device
+ * by the first call on that device (make that first call before any stream
+ * capture).  Every call shares the array and overwrites what the previous
+ * call left there; calls whose work overlaps on the same GPU race and must
+ * not be issued concurrently.  Arguments as for krylov_solve; b and x are
+ * device arrays of 2n doubles, x holds the initial guess.
+ * Errors: SS_ERR_INVALID when n > SS_NOALLOC_MAX_N (use krylov_solve), plus
+ * the statuses of krylov_solve.  The paper has no counterpart of this entry
+ * point; it is an interface variant of the BiCGSTAB solve. */
+ss_status krylov_solve_noalloc(ss_ctx ctx, ss_mat A, ss_prec M, const double* b, double* x, double tol,
+                               int maxiter, int* iters_out, double* resid_out);
+
 /* Full steady-state solve.  H and c_ops as for assemble_liouvillian.
  * rho_out: d*d complex (2 d^2 doubles), column-major, trace-normalised;
  * host memory if rho_on_device == 0, device memory otherwise.  info may be

@@ -23,7 +23,9 @@ from . import _binding as B
 __all__ = ["SolverError", "Context", "Matrix", "Preconditioner", "get_context", "assemble_liouvillian",
            "add_trace_row", "add_shift", "rcm_permute", "permute", "bandwidth_profile", "ilu_factor",
            "spmv", "spmv_f32", "precond_apply", "precond_apply_f32", "krylov_solve", "steady_state",
-           "steady_state_batched", "library_path"]
+           "steady_state_batched", "krylov_solve_noalloc", "NOALLOC_MAX_N", "library_path"]
+
+NOALLOC_MAX_N = 65536
 
 
 def library_path() -> str:
@@ -322,6 +324,19 @@ def steady_state_batched(systems: Sequence, method: str = "iterative-bicgstab", 
         ctx.check(st, "steady_state_batched")
     d = [h.view.n_rows for h, _ in hosts]
     return [r.reshape((dk, dk), order="F") for r, dk in zip(rhos, d)], [infos[k].as_dict() for k in range(ns)]
+
+
+def krylov_solve_noalloc(A: Matrix, M: Preconditioner, b, x, tol: float = 1e-12, maxiter: int = 1000):
+    """BiCGSTAB on A x = b in place on the caller's x, without any allocation
+    inside the call (for callers that cannot allocate; n <= NOALLOC_MAX_N).
+    Returns (status, iters, resid); x holds the initial guess on entry."""
+    n = A.shape[0]
+    it, res = C.c_int(), C.c_double()
+    st = B.load().krylov_solve_noalloc(A.ctx.handle, A.handle, M.handle, _dev_ptr(b, "c128", n),
+                                       _dev_ptr(x, "c128", n), tol, maxiter, C.byref(it), C.byref(res))
+    if st not in (B.SS_OK, B.SS_NOT_CONVERGED, B.SS_BREAKDOWN):
+        A.ctx.check(st, "krylov_solve_noalloc")
+    return st, it.value, res.value
 
 
 def steady_state(H, c_ops: Sequence, method: str = "iterative-bicgstab", tol: float = 1e-10,

@@ -87,6 +87,7 @@ _SIGNATURES = {
     "ss_profile_enable": (C.c_int, [_P, C.c_int]),
     "ss_profile_read": (C.c_int, [_P, C.c_int, _I64P, _DP]),
     "ss_launch_count": (C.c_ulonglong, []),
+    "krylov_solve_noalloc": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int, C.POINTER(C.c_int), _DP]),
     "steady_state": (C.c_int, [_P, C.POINTER(CsrView), C.c_int, C.POINTER(CsrView), C.POINTER(Options),
                                _P, C.c_int, C.POINTER(Info)]),
 }
