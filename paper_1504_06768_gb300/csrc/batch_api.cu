@@ -20,6 +20,11 @@ double now_ms() {
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
+struct PackedDev {                        // device arrays of one packed operand (per pattern)
+    int32_t *rows = nullptr, *col = nullptr, *src = nullptr, *ovb = nullptr, *ove = nullptr, *lvl = nullptr;
+    int32_t nunits = 0, G = 1, E = 1, nlev = 0;
+};
+
 struct Pattern {                          // per distinct pattern of L~ (before ordering)
     std::vector<int32_t> rp, col;         // natural-order pattern (for exact comparison)
     std::vector<int32_t> perm, iperm, tidx;
@@ -29,6 +34,7 @@ struct Pattern {                          // per distinct pattern of L~ (before 
     int32_t *perm_d = nullptr, *tidx_d = nullptr, *dpos_d = nullptr;
     int32_t *lo_units = nullptr, *up_units = nullptr, *lvl_ptr = nullptr, *lvl_rows = nullptr;
     int32_t lo_nunits = 0, up_nunits = 0, lo_g = 1, up_g = 1, a_g = 1, n_levels = 0, up_levels = 0;
+    PackedDev lo, up, pa;
 };
 
 uint64_t fnv1a(const std::vector<int32_t>& a, uint64_t h) {
@@ -43,6 +49,61 @@ int lanes_for(double avg) {
     int g = 1;
     while (g < 32 && 2.0 * g < avg) g <<= 1;
     return g;
+}
+
+// Lane-major packing of one CSR operand (see PackedOp): unit_rows holds R = 32/G
+// row ids per unit; range(i) gives the CSR range [s, e) of row i's entries.
+struct PackedHost {
+    std::vector<int32_t> rows, col, src, ovb, ove, lvl;
+    int32_t nunits = 0, G = 1, E = 1, nlev = 0;
+};
+
+// First unit of each level when each level's rows are cut into units of R.
+std::vector<int32_t> unit_levels(const std::vector<int32_t>& lptr, int R) {
+    std::vector<int32_t> lvl(1, 0);
+    for (size_t l = 0; l + 1 < lptr.size(); ++l) lvl.push_back(lvl.back() + (lptr[l + 1] - lptr[l] + R - 1) / R);
+    return lvl;
+}
+
+template <class F>
+void pack_host(const std::vector<int32_t>& unit_rows, int G, const std::vector<int32_t>& pcol, F range,
+               PackedHost& P) {
+    const int R = 32 / G;
+    P.G = G;
+    P.nunits = (int32_t)(unit_rows.size() / R);
+    std::vector<int32_t> lens;
+    for (int32_t i : unit_rows)
+        if (i >= 0) {
+            auto se = range(i);
+            lens.push_back(se.second - se.first);
+        }
+    std::sort(lens.begin(), lens.end());
+    const int32_t p99 = lens.empty() ? 1 : lens[(size_t)(0.99 * (double)(lens.size() - 1))];
+    P.E = std::max(1, std::min(4, (p99 + G - 1) / G));
+    P.rows = unit_rows;
+    const size_t slots = (size_t)P.nunits * P.E * 32;
+    P.col.assign(slots, -1);
+    P.src.assign(slots, -1);
+    P.ovb.assign(unit_rows.size(), 0);
+    P.ove.assign(unit_rows.size(), 0);
+    for (int32_t u = 0; u < P.nunits; ++u)
+        for (int g = 0; g < R; ++g) {
+            const int32_t i = unit_rows[(size_t)u * R + g];
+            if (i < 0) continue;
+            auto se = range(i);
+            const int32_t s = se.first, e = se.second;
+            for (int sub = 0; sub < G; ++sub)
+                for (int q = 0; q < P.E; ++q) {
+                    const int32_t k = s + sub + q * G;
+                    if (k >= e) continue;
+                    const size_t slot = ((size_t)u * P.E + q) * 32 + (size_t)g * G + sub;
+                    P.col[slot] = pcol[k];
+                    P.src[slot] = k;
+                }
+            const int32_t pe = s + P.E * G;
+            P.ovb[(size_t)u * R + g] = std::min(pe, e);
+            P.ove[(size_t)u * R + g] = e;
+        }
 }
 
 template <class T>
@@ -91,6 +152,36 @@ ss_status build_pattern(ss_ctx ctx, Pattern& P, const DeviceCSR& A, int64_t d, i
     level_units_host(uorder, uptr, 32 / P.up_g, uunits);
     P.lo_nunits = (int32_t)(lunits.size() / (32 / P.lo_g));
     P.up_nunits = (int32_t)(uunits.size() / (32 / P.up_g));
+    // packed operands: the two triangles (level-aligned units) and A (consecutive rows)
+    PackedHost hl, hu, ha;
+    pack_host(lunits, P.lo_g, pcol, [&](int32_t i) { return std::make_pair(prp[i], dpos[i]); }, hl);
+    pack_host(uunits, P.up_g, pcol, [&](int32_t i) { return std::make_pair(dpos[i] + 1, prp[i + 1]); }, hu);
+    hl.lvl = unit_levels(lptr, 32 / P.lo_g);
+    hu.lvl = unit_levels(uptr, 32 / P.up_g);
+    hl.nlev = (int32_t)hl.lvl.size() - 1;
+    hu.nlev = (int32_t)hu.lvl.size() - 1;
+    {
+        const int R = 32 / P.a_g;
+        std::vector<int32_t> arows(((n + R - 1) / R) * R, -1);
+        for (int64_t i = 0; i < n; ++i) arows[i] = (int32_t)i;
+        pack_host(arows, P.a_g, pcol, [&](int32_t i) { return std::make_pair(prp[i], prp[i + 1]); }, ha);
+    }
+    auto up_packed = [&](PackedHost& h, PackedDev& dv) -> ss_status {
+        dv.nunits = h.nunits;
+        dv.G = h.G;
+        dv.E = h.E;
+        SS_TRY(upload_vec(ctx, h.rows, &dv.rows));
+        SS_TRY(upload_vec(ctx, h.col, &dv.col));
+        SS_TRY(upload_vec(ctx, h.src, &dv.src));
+        SS_TRY(upload_vec(ctx, h.ovb, &dv.ovb));
+        SS_TRY(upload_vec(ctx, h.ove, &dv.ove));
+        dv.nlev = h.nlev;
+        if (h.nlev > 0) SS_TRY(upload_vec(ctx, h.lvl, &dv.lvl));
+        return SS_OK;
+    };
+    SS_TRY(up_packed(hl, P.lo));
+    SS_TRY(up_packed(hu, P.up));
+    SS_TRY(up_packed(ha, P.pa));
     SS_TRY(upload_vec(ctx, P.perm, &P.perm_d));
     SS_TRY(upload_vec(ctx, P.tidx, &P.tidx_d));
     SS_TRY(upload_vec(ctx, dpos, &P.dpos_d));
@@ -101,7 +192,19 @@ ss_status build_pattern(ss_ctx ctx, Pattern& P, const DeviceCSR& A, int64_t d, i
     return SS_OK;
 }
 
+void free_packed(ss_ctx ctx, PackedDev& d) {
+    dev_free(ctx, d.rows);
+    dev_free(ctx, d.col);
+    dev_free(ctx, d.src);
+    dev_free(ctx, d.ovb);
+    dev_free(ctx, d.ove);
+    dev_free(ctx, d.lvl);
+}
+
 void free_pattern(ss_ctx ctx, Pattern& P) {
+    free_packed(ctx, P.lo);
+    free_packed(ctx, P.up);
+    free_packed(ctx, P.pa);
     dev_free(ctx, P.perm_d);
     dev_free(ctx, P.tidx_d);
     dev_free(ctx, P.dpos_d);
@@ -220,8 +323,11 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
         b.factor_on_device = 1;
         const size_t inner = mixed ? sizeof(float2) : sizeof(double2);
         char* blk = nullptr;
+        const size_t pk_slots = ((size_t)P.lo.nunits * P.lo.E + (size_t)P.up.nunits * P.up.E +
+                                 (size_t)P.pa.nunits * P.pa.E) * 32;
         const size_t bytes = nnz * sizeof(double2) + n * sizeof(double2) + (mixed ? 2 * nnz * sizeof(float2) + n * sizeof(float2) : 0) +
-                             10 * n * inner + 2 * n * sizeof(double2) + (rho_on_device ? 0 : n * sizeof(double2)) + 256;
+                             10 * n * inner + 2 * n * sizeof(double2) + (rho_on_device ? 0 : n * sizeof(double2)) +
+                             pk_slots * inner + 8 * 256;
         BSTEP(dev_alloc(ctx, reinterpret_cast<void**>(&blk), bytes));
         owned.push_back(blk);
         size_t off = 0;
@@ -238,13 +344,22 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
         b.r64 = reinterpret_cast<double2*>(take(n * sizeof(double2)));
         b.rho_out = rho_on_device ? reinterpret_cast<double2*>(rho_out[fastidx[q]])
                                   : reinterpret_cast<double2*>(take(n * sizeof(double2)));
-        b.lo_units = P.lo_units;
-        b.up_units = P.up_units;
-        b.lo_nunits = P.lo_nunits;
-        b.up_nunits = P.up_nunits;
-        b.lo_g = P.lo_g;
-        b.up_g = P.up_g;
-        b.a_g = P.a_g;
+        auto set_op = [&](PackedOp& o, const PackedDev& dv) {
+            o.rows = dv.rows;
+            o.col = dv.col;
+            o.src = dv.src;
+            o.ovb = dv.ovb;
+            o.ove = dv.ove;
+            o.nunits = dv.nunits;
+            o.G = dv.G;
+            o.E = dv.E;
+            o.lvl = dv.lvl;
+            o.nlev = dv.nlev;
+            o.val = take((size_t)dv.nunits * dv.E * 32 * inner);
+        };
+        set_op(b.lo, P.lo);
+        set_op(b.up, P.up);
+        set_op(b.pa, P.pa);
         b.lvl_ptr = P.lvl_ptr;
         b.lvl_rows = P.lvl_rows;
         b.n_levels = P.n_levels;

@@ -3,12 +3,12 @@
 // CTA: the SpMV, the two triangular solves of M^{-1} (section "Iterative
 // solvers"), the inner products and the vector updates.
 //
-// Triangular solves work in place on one shared-memory vector: rows are
-// grouped into level-aligned units of 32/G rows (G lanes per row); warp w takes
-// units w, w + W, w + 2W, ... in order and each row waits on the shared-memory
-// completion flags of the rows it depends on.  A row only depends on rows of
-// earlier levels, i.e. on earlier units, which their warps process in order,
-// so the earliest unfinished unit can always proceed.  Every wait is bounded.
+// Triangular solves work in place on one shared-memory vector, one level at a
+// time with a barrier between levels: rows are grouped into level-aligned
+// units of 32/G rows (G lanes per row) stored in a packed lane-major layout
+// (one coalesced load per unit and entry slot), and each warp loads its unit
+// of the next level before the barrier.  Nothing in the kernel waits on a
+// flag.
 //
 // FP64 mode: BiCGSTAB in complex FP64 with the acceptance loop of the
 // single-system driver.  Mixed mode: FP32 matrix, factors and Krylov vectors
@@ -24,7 +24,6 @@ namespace {
 constexpr int BT = BATCH_THREADS;
 constexpr int NW = BT / 32;
 constexpr unsigned FULLM = 0xffffffffu;
-constexpr long long SPIN_LIMIT = 1ll << 22;   // with back-off: a wait gives up after ~0.3 s
 
 // ------------------------------------------------------------ arithmetic
 __device__ __forceinline__ double2 D(double2 a) { return a; }
@@ -55,25 +54,47 @@ template <class T> __device__ __forceinline__ T zero();
 template <> __device__ __forceinline__ double2 zero<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 zero<float2>() { return make_float2(0.f, 0.f); }
 
-// Block-wide sums of NV doubles, broadcast to every thread (fixed order).
-template <int NV>
-__device__ void cta_sum(double (&v)[NV], double* red) {
+// Block-wide sums of NV values (A = float or double), returned in double to
+// every thread.  Warp sums by shuffles, then warp 0 adds the NW warp sums in a
+// fixed order and broadcasts them through shared memory (the FP64 pipe is
+// scarce on GB300: the final sum is done once, not by every thread).
+template <int NV, class A>
+__device__ void cta_sum(A (&v)[NV], double (&out)[NV], double* red) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k)
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(FULLM, v[k], o);
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) red[w * NV + k] = v[k];
+        for (int k = 0; k < NV; ++k) red[w * NV + k] = (double)v[k];
     __syncthreads();
+    if (w == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double s = 0.0;
-        for (int q = 0; q < NW; ++q) s += red[q * NV + k];
-        v[k] = s;
+        for (int k = 0; k < NV; ++k) {
+            double t = lane < NW ? red[lane * NV + k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(FULLM, t, o);
+            if (lane == 0) red[NW * NV + k] = t;
+        }
     }
     __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = red[NW * NV + k];
+    __syncthreads();
 }
+
+template <int NV>
+__device__ void cta_sum(double (&v)[NV], double* red) {
+    double out[NV];
+    cta_sum<NV, double>(v, out, red);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = out[k];
+}
+
+// Accumulator type of the inner products: the vector type's real type (the
+// FP32 inner solve accumulates each thread's share in FP32).
+template <class T> struct Acc;
+template <> struct Acc<double2> { using type = double; };
+template <> struct Acc<float2> { using type = float; };
 
 __device__ __forceinline__ bool negligible(double2 a, double nu, double nv) {
     double m = hypot(a.x, a.y);
@@ -81,133 +102,176 @@ __device__ __forceinline__ bool negligible(double2 a, double nu, double nv) {
 }
 
 // ------------------------------------------------------ triangular solves
-// Waits (bounded) until fl[j] == epoch.  Idle warps sleep between polls so
-// that the warps doing the work keep the issue slots and the shared-memory
-// pipe.
-__device__ __forceinline__ bool wait_flag(volatile uint32_t* fl, int32_t j, uint32_t epoch) {
-    if (fl[j] == epoch) return true;
-    long long spins = 0;
-    unsigned ns = 8;
-    while (fl[j] != epoch) {
-        __nanosleep(ns);
-        if (ns < 64) ns <<= 1;
-        if (++spins > SPIN_LIMIT) return false;
+constexpr int MAXE = 3;    // packed entries per lane and unit
+
+// One unit of a packed operand held in registers (a lane's slots, the row
+// and its CSR tail).
+template <class T>
+struct UnitRegs {
+    int32_t jj[MAXE];
+    T vv[MAXE];
+    int32_t i, ob, oe;
+};
+
+template <int G, class T>
+__device__ __forceinline__ void load_unit(const PackedOp& P, int32_t u, int lane, UnitRegs<T>& r) {
+    constexpr int R = 32 / G;
+    const T* __restrict__ pv = reinterpret_cast<const T*>(P.val);
+    const int E = P.E;
+    const int grp = lane / G;
+    r.i = -1;
+    r.ob = r.oe = 0;
+#pragma unroll
+    for (int q = 0; q < MAXE; ++q) {
+        r.jj[q] = -1;
+        r.vv[q] = zero<T>();
     }
-    return true;
+    if (u >= P.nunits) return;
+    r.i = P.rows[u * R + grp];
+#pragma unroll
+    for (int q = 0; q < MAXE; ++q)
+        if (q < E) {
+            const int64_t slot = ((int64_t)u * E + q) * 32 + lane;
+            r.jj[q] = P.col[slot];
+            r.vv[q] = pv[slot];
+        }
+    r.ob = P.ovb[u * R + grp];
+    r.oe = P.ove[u * R + grp];
+}
+
+// In-place triangular solve on the shared vector buf using the packed
+// operand P, one level at a time: the units of a level are spread over the
+// warps, a barrier separates levels, so every dependency of a row is complete
+// when its level starts and nothing waits on a flag.  LOWER: x_i = b_i -
+// sum_{j<i} l_ij x_j; UPPER: x_i = (b_i - sum_{j>i} u_ij x_j) / u_ii.
+// ocol/oval: the CSR of the factors for the entries of long rows that are not
+// packed.  Each warp loads its unit of the next level before the barrier.
+template <bool LOWER, int G, class T>
+__device__ __forceinline__ void solve_unit(const UnitRegs<T>& cu, const int32_t* __restrict__ ocol,
+                                           const T* __restrict__ oval, const T* __restrict__ inv, T* buf,
+                                           int sub) {
+    T dinv = zero<T>();
+    if (!LOWER && cu.i >= 0 && sub == 0) dinv = inv[cu.i];
+    T acc = zero<T>();
+#pragma unroll
+    for (int q = 0; q < MAXE; ++q)
+        if (cu.jj[q] >= 0) acc = fmac(cu.vv[q], buf[cu.jj[q]], acc);
+    for (int32_t k = cu.ob + sub; k < cu.oe; k += G) acc = fmac(oval[k], buf[ocol[k]], acc);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        T other = shd(acc, o);
+        acc.x += other.x;
+        acc.y += other.y;
+    }
+    if (cu.i >= 0 && sub == 0) {
+        T xi = subc(buf[cu.i], acc);
+        if (!LOWER) xi = mulc(xi, dinv);
+        buf[cu.i] = xi;
+    }
 }
 
 template <bool LOWER, int G, class T>
-__device__ void cta_trsv_g(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, const T* __restrict__ val,
-                           const int32_t* __restrict__ dpos, const T* __restrict__ inv,
-                           const int32_t* __restrict__ units, int32_t nunits, T* buf, volatile uint32_t* fl,
-                           uint32_t epoch, int* err) {
-    constexpr int R = 32 / G;
-    constexpr int MAXE = 4;            // entries per lane held in registers before waiting
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane / G, sub = lane % G;
-    for (int32_t u = warp; u < nunits; u += NW) {
-        const int32_t i = units[u * R + grp];
-        int32_t s = 0, e = 0;
-        if (i >= 0) {
-            if (LOWER) { s = rp[i]; e = dpos[i]; }
-            else { s = dpos[i] + 1; e = rp[i + 1]; }
+__device__ void cta_trsv_pk(const PackedOp& P, const int32_t* __restrict__ ocol, const T* __restrict__ oval,
+                            const T* __restrict__ inv, T* buf) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane % G;
+    UnitRegs<T> ua, ub;
+    int32_t beg = P.lvl[0], end = P.lvl[1];
+    load_unit<G, T>(P, beg + warp < end ? beg + warp : P.nunits, lane, ua);
+    for (int32_t l = 0; l < P.nlev; ++l) {
+        const int32_t nb = end, ne = (l + 1 < P.nlev) ? P.lvl[l + 2] : end;
+        // the first unit of the next level for this warp, in flight during this level
+        load_unit<G, T>(P, nb + warp < ne ? nb + warp : P.nunits, lane, ub);
+        solve_unit<LOWER, G, T>(ua, ocol, oval, inv, buf, sub);
+        for (int32_t u = beg + warp + NW; u < end; u += NW) {      // wide levels: more units per warp
+            UnitRegs<T> uc;
+            load_unit<G, T>(P, u, lane, uc);
+            solve_unit<LOWER, G, T>(uc, ocol, oval, inv, buf, sub);
         }
-        int32_t jj[MAXE];
-        T vv[MAXE];
-#pragma unroll
-        for (int q = 0; q < MAXE; ++q) {
-            const int32_t k = s + sub + q * G;
-            const bool ok = k < e;
-            jj[q] = ok ? col[k] : -1;
-            vv[q] = ok ? val[k] : zero<T>();
-        }
-        bool bad = false;
-#pragma unroll
-        for (int q = 0; q < MAXE; ++q)
-            if (jj[q] >= 0 && !wait_flag(fl, jj[q], epoch)) bad = true;
-        __threadfence_block();
-        T acc = zero<T>();
-#pragma unroll
-        for (int q = 0; q < MAXE; ++q)
-            if (jj[q] >= 0) acc = fmac(vv[q], buf[jj[q]], acc);
-        for (int32_t k = s + sub + MAXE * G; k < e; k += G) {      // long rows
-            const int32_t j = col[k];
-            if (!wait_flag(fl, j, epoch)) bad = true;
-            __threadfence_block();
-            acc = fmac(val[k], buf[j], acc);
-        }
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            T other = shd(acc, o);
-            acc.x += other.x;
-            acc.y += other.y;
-        }
-        if (bad) atomicExch(err, 1);
-        if (i >= 0 && sub == 0) {
-            T xi = subc(buf[i], acc);
-            if (!LOWER) xi = mulc(xi, inv[i]);
-            buf[i] = xi;
-            __threadfence_block();
-            fl[i] = epoch;
-        }
+        __syncthreads();
+        ua = ub;
+        beg = nb;
+        end = ne;
     }
-    __syncthreads();
 }
 
 template <bool LOWER, class T>
-__device__ void cta_trsv(int g, const int32_t* rp, const int32_t* col, const T* val, const int32_t* dpos,
-                         const T* inv, const int32_t* units, int32_t nunits, T* buf, volatile uint32_t* fl,
-                         uint32_t epoch, int* err) {
-    switch (g) {
-        case 1: cta_trsv_g<LOWER, 1, T>(rp, col, val, dpos, inv, units, nunits, buf, fl, epoch, err); break;
-        case 2: cta_trsv_g<LOWER, 2, T>(rp, col, val, dpos, inv, units, nunits, buf, fl, epoch, err); break;
-        case 4: cta_trsv_g<LOWER, 4, T>(rp, col, val, dpos, inv, units, nunits, buf, fl, epoch, err); break;
-        case 8: cta_trsv_g<LOWER, 8, T>(rp, col, val, dpos, inv, units, nunits, buf, fl, epoch, err); break;
-        case 16: cta_trsv_g<LOWER, 16, T>(rp, col, val, dpos, inv, units, nunits, buf, fl, epoch, err); break;
-        default: cta_trsv_g<LOWER, 32, T>(rp, col, val, dpos, inv, units, nunits, buf, fl, epoch, err); break;
+__device__ void cta_trsv(const PackedOp& P, const int32_t* ocol, const T* oval, const T* inv, T* buf) {
+    switch (P.G) {
+        case 1: cta_trsv_pk<LOWER, 1, T>(P, ocol, oval, inv, buf); break;
+        case 2: cta_trsv_pk<LOWER, 2, T>(P, ocol, oval, inv, buf); break;
+        case 4: cta_trsv_pk<LOWER, 4, T>(P, ocol, oval, inv, buf); break;
+        case 8: cta_trsv_pk<LOWER, 8, T>(P, ocol, oval, inv, buf); break;
+        case 16: cta_trsv_pk<LOWER, 16, T>(P, ocol, oval, inv, buf); break;
+        default: cta_trsv_pk<LOWER, 32, T>(P, ocol, oval, inv, buf); break;
     }
 }
 
 // ------------------------------------------------------------------ SpMV
-// y = A x with x in shared memory; accumulates <rhat, y> (dots 0, 1) and
-// |y|^2 (dot 2) when rhat is given.
-template <int G, class T>
-__device__ void cta_spmv_g(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, const T* __restrict__ val,
-                           int32_t n, const T* xs, T* __restrict__ y, const T* __restrict__ rhat, double (&dots)[3]) {
-    const int lane = threadIdx.x & 31, sub = lane % G;
-    const int32_t rows_per_pass = BT / G;
-    for (int32_t base = 0; base < n; base += rows_per_pass) {
-        const int32_t r = base + threadIdx.x / G;
-        T acc = zero<T>();
-        if (r < n)
-            for (int32_t k = rp[r] + sub; k < rp[r + 1]; k += G) acc = fmac(val[k], xs[col[k]], acc);
+// y = A x with x in shared memory, from the packed operand (consecutive
+// units); accumulates <rhat, y> (dots 0, 1) and |y|^2 (dot 2) when rhat is
+// given.
+constexpr int SPMV_UNROLL = 4;   // units a warp loads before it consumes any
+constexpr int VU = 2;            // vector elements a thread loads before it computes
+
+template <int G, class T, class A>
+__device__ void cta_spmv_pk(const PackedOp& P, const int32_t* __restrict__ ocol, const T* __restrict__ oval,
+                            const T* xs, T* __restrict__ y, const T* __restrict__ rhat, A (&dots)[3]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane % G;
+    for (int32_t base = warp; base < P.nunits; base += NW * SPMV_UNROLL) {
+        UnitRegs<T> ur[SPMV_UNROLL];
+        T hr[SPMV_UNROLL];
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            T other = shd(acc, o);
-            acc.x += other.x;
-            acc.y += other.y;
+        for (int k = 0; k < SPMV_UNROLL; ++k) {
+            load_unit<G, T>(P, base + k * NW, lane, ur[k]);
+            hr[k] = (rhat && ur[k].i >= 0 && sub == 0) ? rhat[ur[k].i] : zero<T>();
         }
-        if (r < n && sub == 0) {
-            y[r] = acc;
-            if (rhat) {
-                double2 a = D(acc), h = D(rhat[r]);
-                dots[0] += h.x * a.x + h.y * a.y;
-                dots[1] += h.x * a.y - h.y * a.x;
-                dots[2] += a.x * a.x + a.y * a.y;
+#pragma unroll
+        for (int k = 0; k < SPMV_UNROLL; ++k) {
+            T acc = zero<T>();
+#pragma unroll
+            for (int q = 0; q < MAXE; ++q)
+                if (ur[k].jj[q] >= 0) acc = fmac(ur[k].vv[q], xs[ur[k].jj[q]], acc);
+            for (int32_t kk = ur[k].ob + sub; kk < ur[k].oe; kk += G) acc = fmac(oval[kk], xs[ocol[kk]], acc);
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) {
+                T other = shd(acc, o);
+                acc.x += other.x;
+                acc.y += other.y;
+            }
+            const int32_t r = ur[k].i;
+            if (r >= 0 && sub == 0) {
+                y[r] = acc;
+                if (rhat) {
+                    dots[0] += (A)hr[k].x * (A)acc.x + (A)hr[k].y * (A)acc.y;
+                    dots[1] += (A)hr[k].x * (A)acc.y - (A)hr[k].y * (A)acc.x;
+                    dots[2] += (A)acc.x * (A)acc.x + (A)acc.y * (A)acc.y;
+                }
             }
         }
     }
 }
 
-template <class T>
-__device__ void cta_spmv(int g, const int32_t* rp, const int32_t* col, const T* val, int32_t n, const T* xs, T* y,
-                         const T* rhat, double (&dots)[3]) {
-    switch (g) {
-        case 1: cta_spmv_g<1, T>(rp, col, val, n, xs, y, rhat, dots); break;
-        case 2: cta_spmv_g<2, T>(rp, col, val, n, xs, y, rhat, dots); break;
-        case 4: cta_spmv_g<4, T>(rp, col, val, n, xs, y, rhat, dots); break;
-        case 8: cta_spmv_g<8, T>(rp, col, val, n, xs, y, rhat, dots); break;
-        case 16: cta_spmv_g<16, T>(rp, col, val, n, xs, y, rhat, dots); break;
-        default: cta_spmv_g<32, T>(rp, col, val, n, xs, y, rhat, dots); break;
+template <class T, class A>
+__device__ void cta_spmv(const PackedOp& P, const int32_t* ocol, const T* oval, const T* xs, T* y, const T* rhat,
+                         A (&dots)[3]) {
+    switch (P.G) {
+        case 1: cta_spmv_pk<1, T, A>(P, ocol, oval, xs, y, rhat, dots); break;
+        case 2: cta_spmv_pk<2, T, A>(P, ocol, oval, xs, y, rhat, dots); break;
+        case 4: cta_spmv_pk<4, T, A>(P, ocol, oval, xs, y, rhat, dots); break;
+        case 8: cta_spmv_pk<8, T, A>(P, ocol, oval, xs, y, rhat, dots); break;
+        case 16: cta_spmv_pk<16, T, A>(P, ocol, oval, xs, y, rhat, dots); break;
+        default: cta_spmv_pk<32, T, A>(P, ocol, oval, xs, y, rhat, dots); break;
+    }
+}
+
+// Packed values of one operand from the CSR values (gathered once per system).
+template <class T, class V>
+__device__ void cta_pack_values(const PackedOp& P, const V* __restrict__ csr) {
+    T* __restrict__ pv = reinterpret_cast<T*>(P.val);
+    const int64_t total = (int64_t)P.nunits * P.E * 32;
+    for (int64_t s = threadIdx.x; s < total; s += BT) {
+        const int32_t k = P.src[s];
+        pv[s] = k >= 0 ? cvt<T>(D(csr[k])) : zero<T>();
     }
 }
 
@@ -232,11 +296,8 @@ __device__ void cta_prec(Ctx<T>& c, const T* in, T* out) {
     const BatchSys& S = *c.S;
     for (int32_t i = threadIdx.x; i < c.n; i += BT) c.buf[i] = in[i];
     __syncthreads();
-    cta_trsv<true, T>(S.lo_g, S.f_rp, S.f_col, c.fval, S.f_dpos, c.finv, S.lo_units, S.lo_nunits, c.buf, c.fl,
-                      c.epoch, c.err);
-    cta_trsv<false, T>(S.up_g, S.f_rp, S.f_col, c.fval, S.f_dpos, c.finv, S.up_units, S.up_nunits, c.buf, c.fl,
-                       c.epoch + 1, c.err);
-    c.epoch += 2;
+    cta_trsv<true, T>(S.lo, S.f_col, c.fval, c.finv, c.buf);
+    cta_trsv<false, T>(S.up, S.f_col, c.fval, c.finv, c.buf);
     for (int32_t i = threadIdx.x; i < c.n; i += BT) out[i] = c.buf[i];
     // no barrier needed: the shared buffer is only read afterwards
 }
@@ -249,8 +310,24 @@ struct KResult {
 // Right-preconditioned BiCGSTAB on A x = b (x holds the initial guess),
 // stopping at ||b - A x||_2 <= tol.  Same steps and stop/breakdown rules as
 // the multi-kernel solver.
+// re(conj(a) b), im(conj(a) b) and |b|^2 in the accumulator type
+template <class T, class A>
+__device__ __forceinline__ void acc_dot(const T& a, const T& b, A& re, A& im) {
+    re += (A)a.x * (A)b.x + (A)a.y * (A)b.y;
+    im += (A)a.x * (A)b.y - (A)a.y * (A)b.x;
+}
+template <class T, class A>
+__device__ __forceinline__ A norm2(const T& a) {
+    return (A)a.x * (A)a.x + (A)a.y * (A)a.y;
+}
+
+// Right-preconditioned BiCGSTAB on A x = b (x holds the initial guess),
+// stopping at ||b - A x||_2 <= tol.  Same steps and stop/breakdown rules as
+// the multi-kernel solver.  Each thread accumulates its share of an inner
+// product in the vector's precision; the block sums and the scalars are FP64.
 template <class T>
 __device__ KResult cta_bicgstab(Ctx<T>& c, T* x, const T* b, T* wk, double tol, int maxiter) {
+    using A = typename Acc<T>::type;
     const BatchSys& S = *c.S;
     const int32_t n = c.n;
     T* r = wk;
@@ -265,50 +342,74 @@ __device__ KResult cta_bicgstab(Ctx<T>& c, T* x, const T* b, T* wk, double tol, 
     // r = b - A x
     for (int32_t i = threadIdx.x; i < n; i += BT) c.buf[i] = x[i];
     __syncthreads();
-    double dz[3] = {0, 0, 0};
-    cta_spmv<T>(S.a_g, S.a_rp, S.a_col, c.aval, n, c.buf, v, nullptr, dz);
+    A dz[3] = {0, 0, 0};
+    cta_spmv<T>(S.pa, S.a_col, c.aval, c.buf, v, nullptr, dz);
     __syncthreads();
-    double nr[1] = {0.0};
+    A nr[1] = {0};
     for (int32_t i = threadIdx.x; i < n; i += BT) {
         T ri = subc(b[i], v[i]);
         r[i] = ri;
         rhat[i] = ri;
-        double2 q = D(ri);
-        nr[0] += q.x * q.x + q.y * q.y;
+        nr[0] += norm2<T, A>(ri);
     }
-    cta_sum<1>(nr, c.red);
-    double rn = sqrt(nr[0]);
+    double nrs[1];
+    cta_sum<1, A>(nr, nrs, c.red);
+    double rn = sqrt(nrs[0]);
     res.resid = rn;
     if (rn <= tol) { res.status = SS_OK; return res; }
     const double rhat_norm = rn;
-    double2 rho = make_double2(nr[0], 0.0), alpha = make_double2(1, 0), omega = make_double2(1, 0),
+    double2 rho = make_double2(nrs[0], 0.0), alpha = make_double2(1, 0), omega = make_double2(1, 0),
             beta = make_double2(0, 0);
     for (int it = 1; it <= maxiter; ++it) {
         {   // p = r + beta (p - omega v)
             const T bt = cvt<T>(beta), om = cvt<T>(omega);
-            for (int32_t i = threadIdx.x; i < n; i += BT)
-                p[i] = (it == 1) ? r[i] : addc(r[i], mulc(bt, subc(p[i], mulc(om, v[i]))));
+            for (int32_t i0 = threadIdx.x; i0 < n; i0 += VU * BT) {
+                T ra[VU], pa[VU], va[VU];
+#pragma unroll
+                for (int k = 0; k < VU; ++k) {
+                    const int32_t i = i0 + k * BT;
+                    if (i < n) { ra[k] = r[i]; pa[k] = p[i]; va[k] = v[i]; }
+                }
+#pragma unroll
+                for (int k = 0; k < VU; ++k) {
+                    const int32_t i = i0 + k * BT;
+                    if (i < n) p[i] = (it == 1) ? ra[k] : addc(ra[k], mulc(bt, subc(pa[k], mulc(om, va[k]))));
+                }
+            }
         }
         __syncthreads();
         cta_prec<T>(c, p, phat);
-        double dv[3] = {0, 0, 0};
-        cta_spmv<T>(S.a_g, S.a_rp, S.a_col, c.aval, n, c.buf, v, rhat, dv);
-        cta_sum<3>(dv, c.red);
-        const double2 rv = make_double2(dv[0], dv[1]);
-        if (negligible(rv, rhat_norm, sqrt(dv[2]))) { res.status = SS_BREAKDOWN; res.iters = it - 1; return res; }
+        A dv[3] = {0, 0, 0};
+        cta_spmv<T>(S.pa, S.a_col, c.aval, c.buf, v, rhat, dv);
+        double dvs[3];
+        cta_sum<3, A>(dv, dvs, c.red);
+        const double2 rv = make_double2(dvs[0], dvs[1]);
+        if (negligible(rv, rhat_norm, sqrt(dvs[2]))) { res.status = SS_BREAKDOWN; res.iters = it - 1; return res; }
         alpha = cdiv(rho, rv);
-        double ns[1] = {0.0};
+        A ns[1] = {0};
         {
             const T al = cvt<T>(alpha);
-            for (int32_t i = threadIdx.x; i < n; i += BT) {
-                T si = subc(r[i], mulc(al, v[i]));
-                s[i] = si;
-                double2 q = D(si);
-                ns[0] += q.x * q.x + q.y * q.y;
+            for (int32_t i0 = threadIdx.x; i0 < n; i0 += VU * BT) {
+                T ra[VU], va[VU];
+#pragma unroll
+                for (int k = 0; k < VU; ++k) {
+                    const int32_t i = i0 + k * BT;
+                    if (i < n) { ra[k] = r[i]; va[k] = v[i]; }
+                }
+#pragma unroll
+                for (int k = 0; k < VU; ++k) {
+                    const int32_t i = i0 + k * BT;
+                    if (i < n) {
+                        T si = subc(ra[k], mulc(al, va[k]));
+                        s[i] = si;
+                        ns[0] += norm2<T, A>(si);
+                    }
+                }
             }
         }
-        cta_sum<1>(ns, c.red);
-        const double sn = sqrt(ns[0]);
+        double nss[1];
+        cta_sum<1, A>(ns, nss, c.red);
+        const double sn = sqrt(nss[0]);
         if (sn <= tol) {
             const T al = cvt<T>(alpha);
             for (int32_t i = threadIdx.x; i < n; i += BT) x[i] = addc(x[i], mulc(al, phat[i]));
@@ -319,40 +420,60 @@ __device__ KResult cta_bicgstab(Ctx<T>& c, T* x, const T* b, T* wk, double tol, 
             return res;
         }
         cta_prec<T>(c, s, shat);
-        double dt[3] = {0, 0, 0};
-        cta_spmv<T>(S.a_g, S.a_rp, S.a_col, c.aval, n, c.buf, t, nullptr, dt);
+        A dt[3] = {0, 0, 0};
+        cta_spmv<T>(S.pa, S.a_col, c.aval, c.buf, t, nullptr, dt);
         __syncthreads();
-        double tsd[3] = {0, 0, 0};
-        for (int32_t i = threadIdx.x; i < n; i += BT) {
-            double2 a = D(t[i]), q = D(s[i]);
-            tsd[0] += a.x * q.x + a.y * q.y;
-            tsd[1] += a.x * q.y - a.y * q.x;
-            tsd[2] += a.x * a.x + a.y * a.y;
+        A tsd[3] = {0, 0, 0};
+        for (int32_t i0 = threadIdx.x; i0 < n; i0 += VU * BT) {
+            T ta[VU], sa[VU];
+#pragma unroll
+            for (int k = 0; k < VU; ++k) {
+                const int32_t i = i0 + k * BT;
+                if (i < n) { ta[k] = t[i]; sa[k] = s[i]; }
+            }
+#pragma unroll
+            for (int k = 0; k < VU; ++k)
+                if (i0 + k * BT < n) {
+                    acc_dot<T, A>(ta[k], sa[k], tsd[0], tsd[1]);
+                    tsd[2] += norm2<T, A>(ta[k]);
+                }
         }
-        cta_sum<3>(tsd, c.red);
-        if (tsd[2] == 0.0) { res.status = SS_BREAKDOWN; res.iters = it; return res; }
-        omega = make_double2(tsd[0] / tsd[2], tsd[1] / tsd[2]);
-        double nr2[3] = {0, 0, 0};
+        double tss[3];
+        cta_sum<3, A>(tsd, tss, c.red);
+        if (tss[2] == 0.0) { res.status = SS_BREAKDOWN; res.iters = it; return res; }
+        omega = make_double2(tss[0] / tss[2], tss[1] / tss[2]);
+        A nr2[3] = {0, 0, 0};
         {
             const T al = cvt<T>(alpha), om = cvt<T>(omega);
-            for (int32_t i = threadIdx.x; i < n; i += BT) {
-                x[i] = addc(x[i], addc(mulc(al, phat[i]), mulc(om, shat[i])));
-                T ri = subc(s[i], mulc(om, t[i]));
-                r[i] = ri;
-                double2 a = D(rhat[i]), q = D(ri);
-                nr2[0] += a.x * q.x + a.y * q.y;
-                nr2[1] += a.x * q.y - a.y * q.x;
-                nr2[2] += q.x * q.x + q.y * q.y;
+            for (int32_t i0 = threadIdx.x; i0 < n; i0 += VU * BT) {
+                T xa[VU], pa[VU], sa[VU], sha[VU], ta[VU], ha[VU];
+#pragma unroll
+                for (int k = 0; k < VU; ++k) {
+                    const int32_t i = i0 + k * BT;
+                    if (i < n) { xa[k] = x[i]; pa[k] = phat[i]; sha[k] = shat[i]; sa[k] = s[i]; ta[k] = t[i]; ha[k] = rhat[i]; }
+                }
+#pragma unroll
+                for (int k = 0; k < VU; ++k) {
+                    const int32_t i = i0 + k * BT;
+                    if (i < n) {
+                        x[i] = addc(xa[k], addc(mulc(al, pa[k]), mulc(om, sha[k])));
+                        T ri = subc(sa[k], mulc(om, ta[k]));
+                        r[i] = ri;
+                        acc_dot<T, A>(ha[k], ri, nr2[0], nr2[1]);
+                        nr2[2] += norm2<T, A>(ri);
+                    }
+                }
             }
         }
-        cta_sum<3>(nr2, c.red);
-        rn = sqrt(nr2[2]);
+        double nrs2[3];
+        cta_sum<3, A>(nr2, nrs2, c.red);
+        rn = sqrt(nrs2[2]);
         res.iters = it;
         res.resid = rn;
         if (rn <= tol) { res.status = SS_OK; return res; }
         if (omega.x == 0.0 && omega.y == 0.0) { res.status = SS_BREAKDOWN; return res; }
         if (it >= maxiter) { res.status = SS_NOT_CONVERGED; return res; }
-        const double2 rho_new = make_double2(nr2[0], nr2[1]);
+        const double2 rho_new = make_double2(nrs2[0], nrs2[1]);
         if (negligible(rho_new, rhat_norm, rn)) { res.status = SS_BREAKDOWN; return res; }
         beta = cmul(cdiv(rho_new, rho), cdiv(alpha, omega));
         rho = rho_new;
@@ -487,7 +608,50 @@ __device__ void solve_fp64(BatchSys& S, const BatchParams& P, unsigned char* sme
     S.status = status;
 }
 
+// True residual in FP64: r64 = b - A x64 (b = w e_r0), r32 = r64 rounded to
+// FP32; returns ||r64||_2 and, in *lr, ||L rho||_2 for rho = x64 / tr(x64)
+// (L x = b - r64 - w tr(x) e_r0, so no second product is needed).
+__device__ double true_residual(const BatchSys& S, const double2* __restrict__ x64, double2* __restrict__ r64,
+                                float2* __restrict__ r32, double* red, double* lr) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int32_t i = threadIdx.x; i < S.n; i += BT) {
+        double2 y = make_double2(i == S.r0 ? S.w : 0.0, 0.0);
+        for (int32_t k = S.a_rp[i]; k < S.a_rp[i + 1]; ++k) {
+            const double2 a = S.a_val[k], xv = x64[S.a_col[k]];
+            y.x -= a.x * xv.x - a.y * xv.y;
+            y.y -= a.x * xv.y + a.y * xv.x;
+        }
+        r64[i] = y;
+        r32[i] = make_float2((float)y.x, (float)y.y);
+        acc[0] += y.x * y.x + y.y * y.y;
+        if (i < S.d) {
+            const double2 v = x64[S.tidx[i]];
+            acc[1] += v.x;
+            acc[2] += v.y;
+        }
+    }
+    cta_sum<3>(acc, red);
+    const double2 tr = make_double2(acc[1], acc[2]);
+    const double2 y0 = r64[S.r0];
+    const double2 c0 = make_double2(-y0.x + S.w * (1.0 - tr.x), -y0.y - S.w * tr.y);
+    const double l2 = acc[0] - (y0.x * y0.x + y0.y * y0.y) + (c0.x * c0.x + c0.y * c0.y);
+    const double m = hypot(tr.x, tr.y);
+    *lr = m > 0.0 ? sqrt(fmax(l2, 0.0)) / m : INFINITY;
+    return sqrt(acc[0]);
+}
+
+// Mixed precision: one BiCGSTAB whose vectors, matrix, factors and inner
+// products run in FP32 while the iterate x accumulates in FP64.  Whenever the
+// FP32 recursive residual has dropped by DELTA since the last replacement (or
+// every REFRESH iterations), it is replaced by the true FP64 residual
+// b - A x (reliable updating); the solve stops when the FP64 ||L rho||_2 <= tol.
+// A breakdown restarts the recurrence from the current x.
+constexpr double DELTA = 0.05;
+constexpr int REFRESH = 50;
+
 __device__ void solve_mixed(BatchSys& S, const BatchParams& P, unsigned char* smem, double* red, int* err) {
+    using T = float2;
+    using A = float;
     const int32_t n = S.n;
     Ctx<float2> c;
     c.S = &S;
@@ -500,57 +664,134 @@ __device__ void solve_mixed(BatchSys& S, const BatchParams& P, unsigned char* sm
     c.red = red;
     c.epoch = 1;
     c.err = err;
-    for (int32_t i = threadIdx.x; i < n; i += BT) c.fl[i] = 0u;
-    float2* wk = reinterpret_cast<float2*>(S.work);
-    float2* b32 = wk + 8 * (size_t)n;
-    float2* x32 = b32 + n;
+    T* r = reinterpret_cast<float2*>(S.work);
+    T* rhat = r + n;
+    T* p = rhat + n;
+    T* v = p + n;
+    T* s = v + n;
+    T* t = s + n;
+    T* phat = t + n;
+    T* shat = phat + n;
+    T* xd = shat + n;            // FP32 increment of x since the last replacement
     double2* x = S.x64;
-    double2* r = S.r64;
-    for (int32_t i = threadIdx.x; i < n; i += BT) x[i] = make_double2(0.0, 0.0);
-    __syncthreads();
-    int total = 0, status = SS_NOT_CONVERGED, outer = 0;
-    double lr = INFINITY;
-    for (outer = 1; outer <= 30; ++outer) {
-        // FP64 residual r = b - A x and the acceptance test on x
-        double2 tr;
-        lr = (outer == 1) ? INFINITY : cta_lrho(S, x, red, &tr);
-        if (lr <= P.tol) { status = SS_OK; break; }
-        double nrm[1] = {0.0};
-        for (int32_t i = threadIdx.x; i < n; i += BT) {
-            double2 y = make_double2(i == S.r0 ? S.w : 0.0, 0.0);
-            for (int32_t k = S.a_rp[i]; k < S.a_rp[i + 1]; ++k) {
-                const double2 a = S.a_val[k], xv = x[S.a_col[k]];
-                y.x -= a.x * xv.x - a.y * xv.y;
-                y.y -= a.x * xv.y + a.y * xv.x;
-            }
-            r[i] = y;
-            nrm[0] += y.x * y.x + y.y * y.y;
-        }
-        cta_sum<1>(nrm, red);
-        const double rn = sqrt(nrm[0]);
-        if (rn == 0.0) { status = SS_OK; lr = 0.0; break; }
-        if (total >= P.maxiter) break;
-        const double inv = 1.0 / rn;
-        for (int32_t i = threadIdx.x; i < n; i += BT) {
-            b32[i] = make_float2((float)(r[i].x * inv), (float)(r[i].y * inv));
-            x32[i] = make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-        // an FP32 inner solve that stalls above its tolerance returns after a bounded
-        // number of iterations so that the FP64 refinement can continue
-        const int cap = min(P.maxiter - total, max(50, P.maxiter / 5));
-        KResult kr = cta_bicgstab<float2>(c, x32, b32, wk, P.inner_rtol, cap);
-        total += kr.iters;
-        for (int32_t i = threadIdx.x; i < n; i += BT) {
-            x[i].x += rn * (double)x32[i].x;
-            x[i].y += rn * (double)x32[i].y;
-        }
-        __syncthreads();
-        if (kr.status == SS_BREAKDOWN && kr.iters == 0) { status = SS_BREAKDOWN; break; }
+    double2* r64 = S.r64;
+    for (int32_t i = threadIdx.x; i < n; i += BT) {
+        x[i] = make_double2(0.0, 0.0);
+        xd[i] = make_float2(0.f, 0.f);
     }
-    if (outer > 30) outer = 30;
-    S.iters = total;
-    S.outer = outer;
+    __syncthreads();
+    // x += xd in FP64, xd = 0
+    auto fold = [&]() {
+        for (int32_t i = threadIdx.x; i < n; i += BT) {
+            const T d = xd[i];
+            x[i].x += (double)d.x;
+            x[i].y += (double)d.y;
+            xd[i] = make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+    };
+    int it = 0, status = SS_NOT_CONVERGED, restarts = 0, replacements = 0;
+    double lr = INFINITY;
+    while (it < P.maxiter) {
+        // (re)start: true residual, shadow residual r^ = r
+        fold();
+        double rn = true_residual(S, x, r64, r, red, &lr);
+        ++replacements;
+        if (lr <= P.tol) { status = SS_OK; break; }
+        for (int32_t i = threadIdx.x; i < n; i += BT) rhat[i] = r[i];
+        __syncthreads();
+        double rhat_norm = rn, rn_ref = rn;
+        double2 rho = make_double2(rn * rn, 0.0), alpha = make_double2(1, 0), omega = make_double2(1, 0),
+                beta = make_double2(0, 0);
+        bool restart = false;
+        for (int k = 1; it < P.maxiter; ++k) {
+            ++it;
+            {   // p = r + beta (p - omega v)
+                const T bt = cvt<T>(beta), om = cvt<T>(omega);
+                for (int32_t i = threadIdx.x; i < n; i += BT)
+                    p[i] = (k == 1) ? r[i] : addc(r[i], mulc(bt, subc(p[i], mulc(om, v[i]))));
+            }
+            __syncthreads();
+            cta_prec<T>(c, p, phat);
+            A dv[3] = {0, 0, 0};
+            cta_spmv<T>(S.pa, S.a_col, c.aval, c.buf, v, rhat, dv);
+            double dvs[3];
+            cta_sum<3, A>(dv, dvs, c.red);
+            const double2 rv = make_double2(dvs[0], dvs[1]);
+            if (negligible(rv, rhat_norm, sqrt(dvs[2]))) { restart = true; break; }
+            alpha = cdiv(rho, rv);
+            A ns[1] = {0};
+            {
+                const T al = cvt<T>(alpha);
+                for (int32_t i = threadIdx.x; i < n; i += BT) {
+                    T si = subc(r[i], mulc(al, v[i]));
+                    s[i] = si;
+                    ns[0] += norm2<T, A>(si);
+                }
+            }
+            double nss[1];
+            cta_sum<1, A>(ns, nss, c.red);
+            cta_prec<T>(c, s, shat);
+            A dt[3] = {0, 0, 0};
+            cta_spmv<T>(S.pa, S.a_col, c.aval, c.buf, t, nullptr, dt);
+            __syncthreads();
+            A tsd[3] = {0, 0, 0};
+            for (int32_t i = threadIdx.x; i < n; i += BT) {
+                acc_dot<T, A>(t[i], s[i], tsd[0], tsd[1]);
+                tsd[2] += norm2<T, A>(t[i]);
+            }
+            double tss[3];
+            cta_sum<3, A>(tsd, tss, c.red);
+            omega = tss[2] > 0.0 ? make_double2(tss[0] / tss[2], tss[1] / tss[2]) : make_double2(0.0, 0.0);
+            A nr2[3] = {0, 0, 0};
+            {
+                const T al = cvt<T>(alpha), om = cvt<T>(omega);
+                for (int32_t i = threadIdx.x; i < n; i += BT) {
+                    xd[i] = addc(xd[i], addc(mulc(al, phat[i]), mulc(om, shat[i])));
+                    T ri = subc(s[i], mulc(om, t[i]));
+                    r[i] = ri;
+                    acc_dot<T, A>(rhat[i], ri, nr2[0], nr2[1]);
+                    nr2[2] += norm2<T, A>(ri);
+                }
+            }
+            double nrs2[3];
+            cta_sum<3, A>(nr2, nrs2, c.red);
+            double rn32 = sqrt(nrs2[2]);
+            double2 rho_new = make_double2(nrs2[0], nrs2[1]);
+            if (rn32 <= DELTA * rn_ref || k % REFRESH == 0 || tss[2] == 0.0) {
+                fold();
+                rn = true_residual(S, x, r64, r, red, &lr);   // reliable update of r
+                ++replacements;
+                rn_ref = rn;
+                if (lr <= P.tol) { status = SS_OK; break; }
+                A nr3[2] = {0, 0};
+                for (int32_t i = threadIdx.x; i < n; i += BT) acc_dot<T, A>(rhat[i], r[i], nr3[0], nr3[1]);
+                double nrs3[2];
+                cta_sum<2, A>(nr3, nrs3, c.red);
+                rho_new = make_double2(nrs3[0], nrs3[1]);
+                rn32 = rn;
+            }
+            if (tss[2] == 0.0 || (omega.x == 0.0 && omega.y == 0.0) || negligible(rho_new, rhat_norm, rn32)) {
+                restart = true;
+                break;
+            }
+            beta = cmul(cdiv(rho_new, rho), cdiv(alpha, omega));
+            rho = rho_new;
+        }
+        if (status == SS_OK) break;
+        if (restart) {
+            fold();
+            if (++restarts > 8) { status = SS_BREAKDOWN; break; }
+            continue;
+        }
+    }
+    if (status != SS_OK) {       // final acceptance test on the last iterate
+        fold();
+        true_residual(S, x, r64, r, red, &lr);
+        if (lr <= P.tol) status = SS_OK;
+    }
+    S.iters = it;
+    S.outer = replacements;
     S.resid = lr;
     S.status = status;
 }
@@ -568,28 +809,59 @@ __device__ void finalise(const BatchSys& S, double* red) {
     __syncthreads();
 }
 
+template <bool MIXED>
 __global__ void __launch_bounds__(BT, 1) batched_solver(BatchSys* sys, int nsys, BatchParams P, int* queue,
                                                          int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[NW * 3];
+    __shared__ double red[NW * 3 + 3];
     __shared__ int s_idx;
+    // The system's descriptor is copied to shared memory: kept in global
+    // memory, its pointer fields would be re-read from L2 after every store.
+    __shared__ __align__(16) BatchSys S;
     while (true) {
         if (threadIdx.x == 0) s_idx = atomicAdd(queue, 1);
         __syncthreads();
         const int k = s_idx;
         __syncthreads();
         if (k >= nsys) break;
-        BatchSys& S = sys[k];
+        {
+            const int* src = reinterpret_cast<const int*>(&sys[k]);
+            int* dst = reinterpret_cast<int*>(&S);
+            for (int w = threadIdx.x; w < (int)(sizeof(BatchSys) / sizeof(int)); w += BT) dst[w] = src[w];
+        }
+        __syncthreads();
         bool ok = true;
-        if (S.factor_on_device) ok = cta_ilu0(S, P.mixed != 0);
+        if (S.factor_on_device) ok = cta_ilu0(S, MIXED);
         if (!ok) {
-            if (threadIdx.x == 0) { S.status = SS_ZERO_PIVOT; S.iters = 0; S.outer = 0; S.resid = INFINITY; }
+            if (threadIdx.x == 0) {
+                sys[k].status = SS_ZERO_PIVOT;
+                sys[k].iters = 0;
+                sys[k].outer = 0;
+                sys[k].resid = INFINITY;
+            }
             __syncthreads();
             continue;
         }
-        if (P.mixed) solve_mixed(S, P, smem, red, err);
+        if (MIXED) {
+            cta_pack_values<float2>(S.lo, S.f_val32);
+            cta_pack_values<float2>(S.up, S.f_val32);
+            cta_pack_values<float2>(S.pa, S.a_val32);
+        } else {
+            cta_pack_values<double2>(S.lo, S.f_val);
+            cta_pack_values<double2>(S.up, S.f_val);
+            cta_pack_values<double2>(S.pa, S.a_val);
+        }
+        __syncthreads();
+        if (MIXED) solve_mixed(S, P, smem, red, err);
         else solve_fp64(S, P, smem, red, err);
         finalise(S, red);
+        if (threadIdx.x == 0) {
+            sys[k].status = S.status;
+            sys[k].iters = S.iters;
+            sys[k].outer = S.outer;
+            sys[k].resid = S.resid;
+        }
+        __syncthreads();
     }
 }
 
@@ -606,11 +878,15 @@ int batch_max_n(bool mixed) {
 
 ss_status batch_launch(ss_ctx ctx, BatchSys* dsys, int nsys, const BatchParams& p, int max_n, int* queue, int* err) {
     const size_t smem = batch_smem_bytes(max_n, p.mixed != 0);
-    SS_CUDA(ctx, cudaFuncSetAttribute(batched_solver, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = std::max(1, std::min(nsys, ctx->num_sms > 0 ? ctx->num_sms : 1));
-    {
+    if (p.mixed) {
+        SS_CUDA(ctx, cudaFuncSetAttribute(batched_solver<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         ProfScope ps(ctx, PROF_BATCHED);
-        batched_solver<<<(ss_count_launch(), grid), BT, smem, ctx->stream>>>(dsys, nsys, p, queue, err);
+        batched_solver<true><<<(ss_count_launch(), grid), BT, smem, ctx->stream>>>(dsys, nsys, p, queue, err);
+    } else {
+        SS_CUDA(ctx, cudaFuncSetAttribute(batched_solver<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ProfScope ps(ctx, PROF_BATCHED);
+        batched_solver<false><<<(ss_count_launch(), grid), BT, smem, ctx->stream>>>(dsys, nsys, p, queue, err);
     }
     SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;

@@ -8,6 +8,24 @@
 
 constexpr int BATCH_THREADS = 512;
 
+// Lane-major packed layout of one CSR operand (a strict triangle of the
+// factors, or A itself).  Rows are grouped into units of R = 32 / G rows
+// (level-aligned for the triangles, consecutive for A); slot (u*E + q)*32 +
+// lane holds the q-th entry handled by that lane, so a warp reads a whole unit
+// with E coalesced loads.  Entries of a long row beyond its first E*G stay in
+// the CSR and are visited from ovb to ove.
+struct PackedOp {
+    const int32_t* rows;    // nunits * R row ids (-1 pads a unit)
+    const int32_t* col;     // nunits * E * 32 column ids (-1: empty slot)
+    const int32_t* src;     // nunits * E * 32 CSR positions of the slots (-1: empty)
+    const int32_t* ovb;     // nunits * R: first CSR position not packed
+    const int32_t* ove;     // nunits * R: end of the row's CSR range
+    void* val;              // per system: nunits * E * 32 values of the inner type
+    int32_t nunits, G, E;
+    const int32_t* lvl;     // triangles: first unit of each level (nlev + 1 entries)
+    int32_t nlev;
+};
+
 struct BatchSys {
     int32_t n, d;
     // system matrix A (RCM-permuted L + wT or L - sigma I)
@@ -24,11 +42,8 @@ struct BatchSys {
     float2* f_val32;
     float2* f_inv32;
     int32_t factor_on_device;   // 1: iLU(0) computed in the kernel from a_val; 0: factors given
-    // level structure
-    const int32_t* lo_units;
-    const int32_t* up_units;
-    int32_t lo_nunits, up_nunits;
-    int32_t lo_g, up_g, a_g;    // lanes per row of the two solves and of the SpMV
+    // packed operands of the two triangular solves and of the SpMV
+    PackedOp lo, up, pa;
     const int32_t* lvl_ptr;     // lower level boundaries in lvl_rows (factorisation schedule)
     const int32_t* lvl_rows;
     int32_t n_levels;
