@@ -1,11 +1,14 @@
 """Benchmark: steady-state solves/s of the driven dissipative Jaynes-Cummings
 workload (cavity cutoff 40 x two-level atom, Hilbert dimension 80, a
-6400 x 6400 complex128 Liouvillian), at ||L rho||_2 <= 1e-10 in FP64.
+6400 x 6400 complex Liouvillian), at ||L rho||_2 <= 1e-10.
 
-One step = one batch of S systems (seeds rank*S .. rank*S+S-1, drive
-E ~ U[0.2, 1.5]) taken through the whole path on the GPU: Kronecker assembly
-of L, trace row of Eq. (linear), RCM ordering, incomplete LU, preconditioned
-Krylov iteration, acceptance test and trace-normalised rho.
+One step = one batch of S systems (default S = 152, one per SM; seeds
+rank*S .. rank*S+S-1, drive E ~ U[0.2, 1.5]) taken through the whole path on
+the GPU by steady_state_batched: Kronecker assembly of L, trace row of
+Eq. (linear), RCM ordering, iLU(0), preconditioned BiCGSTAB, acceptance test
+||L rho||_2 <= 1e-10 and trace-normalised rho.  The headline precision is the
+FP32-inner / FP64-refined path; the same step in FP64 is timed after it
+(`compare`).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
@@ -36,7 +39,7 @@ if ROOT not in sys.path:
 METRIC = "steady-state solves/s at ||L rho||<=1e-10"
 UNIT = "solves/s"
 TOL = 1e-10
-BATCH = 32
+BATCH = 152          # systems per step: one per SM of a GB300 (seeds rank*BATCH ...)
 JC_N = 40
 
 
@@ -111,9 +114,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _systems(rank: int):
+def _systems(rank: int, batch: int):
     from workloads import jaynes_cummings_rwa
-    return [jaynes_cummings_rwa(seed=rank * BATCH + s, N=JC_N) for s in range(BATCH)]
+    return [jaynes_cummings_rwa(seed=rank * batch + s, N=JC_N) for s in range(batch)]
 
 
 # --------------------------------------------------------------------- GPU arm
@@ -137,7 +140,9 @@ def run_gpu(args):
     lib = B.load()
     stream = torch.cuda.current_stream()
     ctx = ss.Context(local, stream)
-    systems = _systems(rank)
+    global BATCH
+    BATCH = args.batch
+    systems = _systems(rank, BATCH)
     d = systems[0].d
     precond = args.precond
 
@@ -234,6 +239,23 @@ def run_gpu(args):
         prof[name] = (cnt.value, ms.value)
     step_infos = list(infos)
     total_ms = sum(times)
+    # the same step in the other precision, for the mixed-versus-FP64 comparison
+    other = None
+    if not args.no_compare:
+        saved = opt.precision
+        opt.precision = B.PRECISIONS["fp64" if args.precision == "mixed" else "mixed"]
+        infos.clear()
+        step()
+        infos.clear()
+        ot = timed(max(1, min(args.steps, 3)))
+        oinf = list(infos)
+        opt.precision = saved
+        oms = sum(ot) / len(ot)
+        other = {"precision": "fp64" if args.precision == "mixed" else "mixed",
+                 "value": BATCH / (oms / 1000.0), "ms_per_step": oms,
+                 "iters_mean": statistics.mean(i["iters"] for i in oinf),
+                 "max_resid_Lrho": max(i["resid_Lrho"] for i in oinf)}
+    infos.clear()
     ms_step = total_ms / args.steps
     if ws > 1:
         import torch.distributed as dist
@@ -298,7 +320,7 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "c64 inner / c128 refined" if args.precision == "mixed" else "c128 (f64)",
         "data": "synthetic",
         "config": {"workload": "jc40: driven dissipative Jaynes-Cummings, cavity 40 x atom, n=6400, "
-                               f"{BATCH} seeds per step (E~U[0.2,1.5])",
+                               f"{BATCH} seeds per step (E~U[0.2,1.5]), one persistent launch per step",
                    "method": args.method, "precond": precond, "precision": args.precision, "ordering": "rcm",
                    "tol": TOL,
                    "batch_per_gpu": BATCH, "parallelism": f"replicas x{ws}",
@@ -308,6 +330,7 @@ def run_gpu(args):
         "roofline": roofline,
         "clocks": clk.summary(),
         "gpu_launches": int(launches),
+        "compare": other,
         "solve": {"iters_mean": statistics.mean(i["iters"] for i in step_infos), "max_resid_Lrho": resid,
                   "nnz": nnz, "nnz_factors": nnzf, "levels": [step_infos[0]["levels_lower"],
                                                                 step_infos[0]["levels_upper"]],
@@ -385,7 +408,9 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--method", default="iterative-bicgstab")
     ap.add_argument("--precond", default="ilu0", choices=["ilu0", "ilut"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

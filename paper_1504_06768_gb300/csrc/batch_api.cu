@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <thread>
 #include <vector>
 
 #include "batched.cuh"
@@ -273,37 +274,90 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
         cudaStreamSynchronize(ctx->stream);
     };
 #define BSTEP(call) do { ss_status _st = (call); if (_st != SS_OK) { cleanup(); return _st; } } while (0)
-    int max_n = 0;
-    for (size_t q = 0; q < fastidx.size(); ++q) {
+    // Setup runs on worker threads, each with its own stream: (A) assembly,
+    // trace row and the pattern of L~; (B, serial) one RCM ordering and level
+    // schedule per distinct pattern; (C) the symmetric permutations.
+    const size_t ns = fastidx.size();
+    const int nthreads = (int)std::max<size_t>(
+        1, std::min<size_t>(ns, std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()))));
+    std::vector<ss_ctx_s> wctx(nthreads);
+    for (auto& w : wctx) {
+        w.device = ctx->device;
+        w.num_sms = ctx->num_sms;
+        SS_CUDA(ctx, cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking));
+    }
+    auto drop_streams = [&]() {
+        for (auto& w : wctx) {
+            cudaStreamSynchronize(w.stream);
+            cudaStreamDestroy(w.stream);
+        }
+    };
+    std::vector<std::vector<int32_t>> prps(ns), pcols(ns);
+    std::vector<ss_status> wst(ns, SS_OK);
+    std::vector<std::string> werr(ns);
+    std::vector<int64_t> dims(ns, 0);
+    auto run_workers = [&](auto&& body) {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nthreads; ++t)
+            th.emplace_back([&, t]() {
+                cudaSetDevice(ctx->device);
+                for (size_t q = t; q < ns; q += nthreads) body(&wctx[t], q);
+                cudaStreamSynchronize(wctx[t].stream);
+            });
+        for (auto& x : th) x.join();
+        for (size_t q = 0; q < ns; ++q)
+            if (wst[q] != SS_OK) return (ss_status)set_error(ctx, wst[q], werr[q]);
+        return SS_OK;
+    };
+    ss_status pst = run_workers([&](ss_ctx wc, size_t q) {
         const int k = fastidx[q];
-        BSTEP(assemble_liouvillian(ctx, &H[k], n_c[k], n_c[k] ? c_ops[k] : nullptr, &sys[q].L));
-        BSTEP(add_trace_row(ctx, sys[q].L, opt.w, &sys[q].A, &sys[q].w));
-        const DeviceCSR& A = sys[q].A->m;
-        std::vector<int32_t> rp(A.n_rows + 1), col(A.nnz);
-        SS_CUDA(ctx, cudaMemcpyAsync(rp.data(), A.row_ptr, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost,
-                                     ctx->stream));
-        SS_CUDA(ctx, cudaMemcpyAsync(col.data(), A.col, sizeof(int32_t) * col.size(), cudaMemcpyDeviceToHost,
-                                     ctx->stream));
-        SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        const uint64_t h = fnv1a(col, fnv1a(rp, 1469598103934665603ull));
+        ss_status st = assemble_liouvillian(wc, &H[k], n_c[k], n_c[k] ? c_ops[k] : nullptr, &sys[q].L);
+        if (st == SS_OK) st = add_trace_row(wc, sys[q].L, opt.w, &sys[q].A, &sys[q].w);
+        if (st == SS_OK) {
+            const DeviceCSR& A = sys[q].A->m;
+            dims[q] = sys[q].L->d;
+            prps[q].resize(A.n_rows + 1);
+            pcols[q].resize(A.nnz);
+            cudaMemcpyAsync(prps[q].data(), A.row_ptr, sizeof(int32_t) * prps[q].size(), cudaMemcpyDeviceToHost,
+                            wc->stream);
+            cudaMemcpyAsync(pcols[q].data(), A.col, sizeof(int32_t) * pcols[q].size(), cudaMemcpyDeviceToHost,
+                            wc->stream);
+            cudaError_t e = cudaStreamSynchronize(wc->stream);
+            if (e != cudaSuccess) st = cuda_check(wc, e, "pattern download");
+        }
+        if (sys[q].L) {
+            ss_mat_free(sys[q].L);
+            sys[q].L = nullptr;
+        }
+        wst[q] = st;
+        if (st != SS_OK) werr[q] = wc->last_error;
+    });
+    if (pst != SS_OK) { drop_streams(); cleanup(); return pst; }
+    int max_n = 0;
+    for (size_t q = 0; q < ns; ++q) {
+        const uint64_t h = fnv1a(pcols[q], fnv1a(prps[q], 1469598103934665603ull));
         int found = -1;
         for (int pi : by_hash[h])
-            if (pats[pi]->rp == rp && pats[pi]->col == col) { found = pi; break; }
+            if (pats[pi]->rp == prps[q] && pats[pi]->col == pcols[q]) { found = pi; break; }
         if (found < 0) {
             pats.emplace_back(new Pattern());
             Pattern& P = *pats.back();
-            P.rp.swap(rp);
-            P.col.swap(col);
-            BSTEP(build_pattern(ctx, P, A, sys[q].L->d, opt.use_rcm));
+            P.rp.swap(prps[q]);
+            P.col.swap(pcols[q]);
+            ss_status st = build_pattern(ctx, P, sys[q].A->m, dims[q], opt.use_rcm);
+            if (st != SS_OK) { drop_streams(); cleanup(); return st; }
             found = (int)pats.size() - 1;
             by_hash[h].push_back(found);
         }
         sys[q].pat = found;
-        BSTEP(permute_impl(ctx, A, pats[found]->perm.data(), sys[q].Ap));
-        ss_mat_free(sys[q].L);
-        sys[q].L = nullptr;
-        max_n = std::max<int>(max_n, (int)A.n_rows);
+        max_n = std::max<int>(max_n, (int)sys[q].A->m.n_rows);
     }
+    pst = run_workers([&](ss_ctx wc, size_t q) {
+        wst[q] = permute_impl(wc, sys[q].A->m, pats[sys[q].pat]->perm.data(), sys[q].Ap);
+        if (wst[q] != SS_OK) werr[q] = wc->last_error;
+    });
+    drop_streams();
+    if (pst != SS_OK) { cleanup(); return pst; }
     // per-system buffers and descriptors
     std::vector<BatchSys> hs(fastidx.size());
     for (size_t q = 0; q < fastidx.size(); ++q) {
