@@ -145,6 +145,19 @@ ss_status assemble_liouvillian(ss_ctx ctx, const ss_csr_view* H, int n_c, const 
  * *w_used (may be NULL).  The right-hand side of Eq. (linear) is w e_0. */
 ss_status add_trace_row(ss_ctx ctx, ss_mat L, double w, ss_mat* out, double* w_used);
 
+/* The trace-row systems of many Liouvillians at once: out[k] receives
+ * L~_k = L_k + w_k T, L_k assembled from H[k] and the n_c[k] operators
+ * c_ops[k] (Eq. lindblad, as assemble_liouvillian) and the trace row added as
+ * add_trace_row does (Eq. linear), with w_k = w when w > 0, else
+ * mean_i |(L_k)_ii|; each is entry for entry the matrix those two calls give.
+ * w_used (may be NULL) receives the n_sys weights.  The operators of all
+ * systems are stacked block-diagonally on the device, so the number of kernel
+ * launches does not grow with n_sys.  out (n_sys handles, caller-allocated
+ * array) is all NULL on failure.  Errors: as assemble_liouvillian; device
+ * views must be 4-byte (indices) and 8-byte (values) aligned. */
+ss_status assemble_trace_batched(ss_ctx ctx, int n_sys, const ss_csr_view* H, const int* n_c,
+                                 const ss_csr_view* const* c_ops, double w, ss_mat* out, double* w_used);
+
 /* Eq. (inverse): L - sigma I.  Every diagonal entry is stored afterwards. */
 ss_status add_shift(ss_ctx ctx, ss_mat L, double sigma, ss_mat* out);
 

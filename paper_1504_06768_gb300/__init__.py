@@ -198,6 +198,38 @@ def add_trace_row(L: Matrix, w: float = 0.0):
     return Matrix(L.ctx, h), wu.value
 
 
+def assemble_trace_batched(systems: Sequence, w: float = 0.0, ctx: Optional[Context] = None):
+    """Eq. (lindblad) and Eq. (linear) for many systems (H, c_ops) in one call:
+    returns a list of (L + w_k T, w_k).  CSR views may be scipy matrices (host)
+    or (row_ptr, col, val, n) tuples of device tensors."""
+    ctx = ctx or get_context()
+    views, keep = [], []
+    for H, cs in systems:
+        hv = _view(H, keep)
+        views.append((hv, [_view(c, keep) for c in cs]))
+    ns = len(views)
+    Hs = (B.CsrView * max(ns, 1))(*[h for h, _ in views])
+    ncs = (C.c_int * max(ns, 1))(*[len(cs) for _, cs in views])
+    carrs = [(B.CsrView * max(len(cs), 1))(*cs) for _, cs in views]
+    cptrs = (C.POINTER(B.CsrView) * max(ns, 1))(*[C.cast(a, C.POINTER(B.CsrView)) for a in carrs])
+    outs = (C.c_void_p * max(ns, 1))()
+    wu = (C.c_double * max(ns, 1))()
+    ctx.check(B.load().assemble_trace_batched(ctx.handle, ns, Hs, ncs, cptrs, w, outs, wu), "assemble_trace_batched")
+    return [(Matrix(ctx, C.c_void_p(outs[k])), wu[k]) for k in range(ns)]
+
+
+def _view(m, keep):
+    """CSR view of a scipy matrix (host) or of a (row_ptr, col, val, n_cols)
+    tuple of device tensors (int32, int32, complex128)."""
+    if isinstance(m, tuple):
+        rp, col, val, n_cols = m
+        keep.append(m)
+        return B.CsrView(rp.numel() - 1, n_cols, val.numel(), rp.data_ptr(), col.data_ptr(), val.data_ptr(), 1)
+    h = _CsrHost(m)
+    keep.append(h)
+    return h.view
+
+
 def add_shift(L: Matrix, sigma: float = 1e-15) -> Matrix:
     """Eq. (inverse): L - sigma I."""
     h = C.c_void_p()

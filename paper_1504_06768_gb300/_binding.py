@@ -63,6 +63,8 @@ _SIGNATURES = {
     "ss_options_default": (None, [C.POINTER(Options)]),
     "assemble_liouvillian": (C.c_int, [_P, C.POINTER(CsrView), C.c_int, C.POINTER(CsrView), _PP]),
     "add_trace_row": (C.c_int, [_P, _P, C.c_double, _PP, _DP]),
+    "assemble_trace_batched": (C.c_int, [_P, C.c_int, C.POINTER(CsrView), C.POINTER(C.c_int),
+                                         C.POINTER(C.POINTER(CsrView)), C.c_double, C.POINTER(C.c_void_p), _DP]),
     "add_shift": (C.c_int, [_P, _P, C.c_double, _PP]),
     "rcm_permute": (C.c_int, [_P, _P, _P, _I64P, _I64P]),
     "permute": (C.c_int, [_P, _P, _P, _PP]),

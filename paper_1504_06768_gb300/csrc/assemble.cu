@@ -155,40 +155,40 @@ struct OpSet {            // per collapse operator: C, C^+C, (C^+C)^T
     CsrRef c, ctc, ctct;
 };
 
-__global__ void lrow_count(CsrRef h, CsrRef ht, const OpSet* __restrict__ ops, int n_c, int64_t d,
-                           int32_t* __restrict__ cnt) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= d * d) return;
-    int64_t i = p % d, j = p / d;
-    int64_t s = (h.rp[i + 1] - h.rp[i]) + (ht.rp[j + 1] - ht.rp[j]);
+// Number of candidates of row (i, j) of L.  gi = row i and gj = row j of the
+// operators, which may be blocks of a block-diagonal stack (see row_build).
+__device__ __forceinline__ int64_t row_count(const CsrRef& h, const CsrRef& ht, const OpSet* __restrict__ ops, int n_c,
+                                             int64_t gi, int64_t gj) {
+    int64_t s = (h.rp[gi + 1] - h.rp[gi]) + (ht.rp[gj + 1] - ht.rp[gj]);
     for (int c = 0; c < n_c; ++c) {
         const OpSet& o = ops[c];
-        s += (int64_t)(o.c.rp[j + 1] - o.c.rp[j]) * (o.c.rp[i + 1] - o.c.rp[i]);
-        s += o.ctc.rp[i + 1] - o.ctc.rp[i];
-        s += o.ctct.rp[j + 1] - o.ctct.rp[j];
+        s += (int64_t)(o.c.rp[gj + 1] - o.c.rp[gj]) * (o.c.rp[gi + 1] - o.c.rp[gi]);
+        s += o.ctc.rp[gi + 1] - o.ctc.rp[gi];
+        s += o.ctct.rp[gj + 1] - o.ctct.rp[gj];
     }
-    cnt[p] = (int32_t)s;
+    return s;
 }
 
+// Candidates of row p = i + d j of L, written from key/val[base], sorted and
+// summed in place; returns the number of stored (non-zero) entries, whose keys
+// are then the column indices.  The operators' rows and columns are offset by
+// doff (a system inside a block-diagonal stack; 0 for a single system).
 // Candidate key = column * T + term, T = 2 + 3 n_c.  Terms: 0 (+H_ik),
 // 1 (H_lj, subtracted), 2 + 3c + {0: conj(C_jl) C_ik, 1: (C^+C)_ik, 2: (C^+C)_lj}.
-__global__ void lrow_build(CsrRef h, CsrRef ht, const OpSet* __restrict__ ops, int n_c, int64_t d,
-                           const int32_t* __restrict__ off, unsigned long long* __restrict__ key,
-                           double2* __restrict__ val, int32_t* __restrict__ outcnt) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t n = d * d;
-    if (p >= n) return;
+__device__ int32_t row_build(const CsrRef& h, const CsrRef& ht, const OpSet* __restrict__ ops, int n_c, int64_t d,
+                             int64_t doff, int64_t i, int64_t j, int32_t base, unsigned long long* __restrict__ key,
+                             double2* __restrict__ val) {
     const unsigned long long T = 2ull + 3ull * (unsigned long long)n_c;
-    int64_t i = p % d, j = p / d;
-    int32_t base = off[p], m = 0;
-    for (int32_t t = h.rp[i]; t < h.rp[i + 1]; ++t) {           // l = j, k = col
-        unsigned long long q = (unsigned long long)(h.col[t] + d * j);
+    const int64_t gi = doff + i, gj = doff + j;
+    int32_t m = 0;
+    for (int32_t t = h.rp[gi]; t < h.rp[gi + 1]; ++t) {         // l = j, k = col
+        unsigned long long q = (unsigned long long)(h.col[t] - doff + d * j);
         key[base + m] = q * T + 0;
         val[base + m] = h.val[t];
         ++m;
     }
-    for (int32_t t = ht.rp[j]; t < ht.rp[j + 1]; ++t) {         // k = i, l = row of H
-        unsigned long long q = (unsigned long long)(i + d * ht.col[t]);
+    for (int32_t t = ht.rp[gj]; t < ht.rp[gj + 1]; ++t) {       // k = i, l = row of H
+        unsigned long long q = (unsigned long long)(i + d * (ht.col[t] - doff));
         key[base + m] = q * T + 1;
         val[base + m] = ht.val[t];
         ++m;
@@ -196,24 +196,24 @@ __global__ void lrow_build(CsrRef h, CsrRef ht, const OpSet* __restrict__ ops, i
     for (int c = 0; c < n_c; ++c) {
         const OpSet& o = ops[c];
         unsigned long long tb = 2ull + 3ull * c;
-        for (int32_t a = o.c.rp[j]; a < o.c.rp[j + 1]; ++a) {
-            int64_t l = o.c.col[a];
+        for (int32_t a = o.c.rp[gj]; a < o.c.rp[gj + 1]; ++a) {
+            int64_t l = o.c.col[a] - doff;
             double2 cj = cconj(o.c.val[a]);                      // conj(C_jl)
-            for (int32_t b = o.c.rp[i]; b < o.c.rp[i + 1]; ++b) {
-                unsigned long long q = (unsigned long long)(o.c.col[b] + d * l);
+            for (int32_t b = o.c.rp[gi]; b < o.c.rp[gi + 1]; ++b) {
+                unsigned long long q = (unsigned long long)(o.c.col[b] - doff + d * l);
                 key[base + m] = q * T + tb;
                 val[base + m] = mul_rn(cj, o.c.val[b]);
                 ++m;
             }
         }
-        for (int32_t t = o.ctc.rp[i]; t < o.ctc.rp[i + 1]; ++t) {
-            unsigned long long q = (unsigned long long)(o.ctc.col[t] + d * j);
+        for (int32_t t = o.ctc.rp[gi]; t < o.ctc.rp[gi + 1]; ++t) {
+            unsigned long long q = (unsigned long long)(o.ctc.col[t] - doff + d * j);
             key[base + m] = q * T + tb + 1;
             val[base + m] = o.ctc.val[t];
             ++m;
         }
-        for (int32_t t = o.ctct.rp[j]; t < o.ctct.rp[j + 1]; ++t) {
-            unsigned long long q = (unsigned long long)(i + d * o.ctct.col[t]);
+        for (int32_t t = o.ctct.rp[gj]; t < o.ctct.rp[gj + 1]; ++t) {
+            unsigned long long q = (unsigned long long)(i + d * (o.ctct.col[t] - doff));
             key[base + m] = q * T + tb + 2;
             val[base + m] = o.ctct.val[t];
             ++m;
@@ -269,7 +269,57 @@ __global__ void lrow_build(CsrRef h, CsrRef ht, const OpSet* __restrict__ ops, i
             ++w;
         }
     }
-    outcnt[p] = w;
+    return w;
+}
+
+__global__ void lrow_count(CsrRef h, CsrRef ht, const OpSet* __restrict__ ops, int n_c, int64_t d,
+                           int32_t* __restrict__ cnt) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= d * d) return;
+    cnt[p] = (int32_t)row_count(h, ht, ops, n_c, p % d, p / d);
+}
+
+__global__ void lrow_build(CsrRef h, CsrRef ht, const OpSet* __restrict__ ops, int n_c, int64_t d,
+                           const int32_t* __restrict__ off, unsigned long long* __restrict__ key,
+                           double2* __restrict__ val, int32_t* __restrict__ outcnt) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= d * d) return;
+    outcnt[p] = row_build(h, ht, ops, n_c, d, 0, p % d, p / d, off[p], key, val);
+}
+
+// Batched forms: the operators of several systems stacked block-diagonally;
+// system s owns operator rows [doff[s], doff[s+1]) and rows
+// [row_off[s], row_off[s+1]) of the concatenated Liouvillians.
+__device__ __forceinline__ int64_t find_system(const int64_t* __restrict__ row_off, int64_t nsys, int64_t p) {
+    int64_t lo = 0, hi = nsys - 1;
+    while (lo < hi) {                      // last s with row_off[s] <= p
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (row_off[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void lrow_count_b(CsrRef h, CsrRef ht, const OpSet* __restrict__ ops, int n_c,
+                             const int64_t* __restrict__ row_off, const int64_t* __restrict__ doff, int64_t nsys,
+                             int32_t reserve_row0, int32_t* __restrict__ cnt) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= row_off[nsys]) return;
+    const int64_t s = find_system(row_off, nsys, p), pl = p - row_off[s];
+    const int64_t d = doff[s + 1] - doff[s];
+    int64_t c = row_count(h, ht, ops, n_c, doff[s] + pl % d, doff[s] + pl / d);
+    if (pl == 0) c += reserve_row0 ? d : 0;
+    cnt[p] = (int32_t)c;
+}
+
+__global__ void lrow_build_b(CsrRef h, CsrRef ht, const OpSet* __restrict__ ops, int n_c,
+                             const int64_t* __restrict__ row_off, const int64_t* __restrict__ doff, int64_t nsys,
+                             const int32_t* __restrict__ off, unsigned long long* __restrict__ key,
+                             double2* __restrict__ val, int32_t* __restrict__ outcnt) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= row_off[nsys]) return;
+    const int64_t s = find_system(row_off, nsys, p), pl = p - row_off[s];
+    const int64_t d = doff[s + 1] - doff[s];
+    outcnt[p] = row_build(h, ht, ops, n_c, d, doff[s], pl % d, pl / d, off[p], key, val);
 }
 
 __global__ void lrow_compact(const int32_t* __restrict__ src_off, const int32_t* __restrict__ dst_off, int64_t n,
@@ -346,29 +396,59 @@ ss_status ctc_csr(ss_ctx ctx, const DeviceCSR& c, const DeviceCSR& ct, DeviceCSR
 
 }  // namespace
 
+namespace {
+
+struct OpPrep {                       // H^T and, per collapse operator, C^T, C^+C, (C^+C)^T
+    DeviceCSR Ht;
+    std::vector<DeviceCSR> Ct, CtC, CtCt;
+    OpSet* dops = nullptr;            // device table of the operator triples
+};
+
+void free_ops(ss_ctx ctx, OpPrep& o) {
+    dev_free(ctx, o.dops);
+    o.dops = nullptr;
+    free_csr(ctx, o.Ht);
+    for (size_t c = 0; c < o.Ct.size(); ++c) {
+        free_csr(ctx, o.Ct[c]);
+        free_csr(ctx, o.CtC[c]);
+        free_csr(ctx, o.CtCt[c]);
+    }
+}
+
+ss_status prep_ops(ss_ctx ctx, const DeviceCSR& H, const std::vector<DeviceCSR>& C, OpPrep& o) {
+    const int n_c = (int)C.size();
+    SS_TRY(transpose_csr(ctx, H, o.Ht));
+    o.Ct.resize(n_c);
+    o.CtC.resize(n_c);
+    o.CtCt.resize(n_c);
+    std::vector<OpSet> hops(n_c);
+    for (int c = 0; c < n_c; ++c) {
+        SS_TRY(transpose_csr(ctx, C[c], o.Ct[c]));
+        SS_TRY(ctc_csr(ctx, C[c], o.Ct[c], o.CtC[c]));
+        SS_TRY(transpose_csr(ctx, o.CtC[c], o.CtCt[c]));
+        hops[c].c = CsrRef{C[c].row_ptr, C[c].col, C[c].val};
+        hops[c].ctc = CsrRef{o.CtC[c].row_ptr, o.CtC[c].col, o.CtC[c].val};
+        hops[c].ctct = CsrRef{o.CtCt[c].row_ptr, o.CtCt[c].col, o.CtCt[c].val};
+    }
+    SS_TRY(dev_alloc_n(ctx, &o.dops, (size_t)(n_c > 0 ? n_c : 1)));
+    if (n_c > 0)
+        SS_CUDA(ctx, cudaMemcpyAsync(o.dops, hops.data(), sizeof(OpSet) * n_c, cudaMemcpyHostToDevice, ctx->stream));
+    return SS_OK;       // (a copy from pageable memory has read hops when the call returns)
+}
+
+}  // namespace
+
 ss_status assemble_impl(ss_ctx ctx, const DeviceCSR& H, const std::vector<DeviceCSR>& C, DeviceCSR& L) {
     L = DeviceCSR();
     const int64_t d = H.n_rows;
     const int64_t n = d * d;
     if (n > INT32_MAX) return set_error(ctx, SS_ERR_UNSUPPORTED, "Liouvillian dimension exceeds 2^31-1");
     const int n_c = (int)C.size();
-
-    DeviceCSR Ht;
-    SS_TRY(transpose_csr(ctx, H, Ht));
-    std::vector<DeviceCSR> Ct(n_c), CtC(n_c), CtCt(n_c);
-    std::vector<OpSet> hops(n_c);
-    for (int c = 0; c < n_c; ++c) {
-        SS_TRY(transpose_csr(ctx, C[c], Ct[c]));
-        SS_TRY(ctc_csr(ctx, C[c], Ct[c], CtC[c]));
-        SS_TRY(transpose_csr(ctx, CtC[c], CtCt[c]));
-        hops[c].c = CsrRef{C[c].row_ptr, C[c].col, C[c].val};
-        hops[c].ctc = CsrRef{CtC[c].row_ptr, CtC[c].col, CtC[c].val};
-        hops[c].ctct = CsrRef{CtCt[c].row_ptr, CtCt[c].col, CtCt[c].val};
-    }
-    OpSet* dops = nullptr;
-    SS_TRY(dev_alloc_n(ctx, &dops, (size_t)(n_c > 0 ? n_c : 1)));
-    if (n_c > 0)
-        SS_CUDA(ctx, cudaMemcpyAsync(dops, hops.data(), sizeof(OpSet) * n_c, cudaMemcpyHostToDevice, ctx->stream));
+    OpPrep o;
+    ss_status st = prep_ops(ctx, H, C, o);
+    if (st != SS_OK) { free_ops(ctx, o); return st; }
+    OpSet* dops = o.dops;
+    const DeviceCSR& Ht = o.Ht;
 
     int32_t *cnt = nullptr, *off = nullptr, *cnt2 = nullptr;
     SS_TRY(dev_alloc_n(ctx, &cnt, (size_t)n + 1));
@@ -398,12 +478,47 @@ ss_status assemble_impl(ss_ctx ctx, const DeviceCSR& H, const std::vector<Device
     dev_free(ctx, cnt);
     dev_free(ctx, off);
     dev_free(ctx, cnt2);
-    dev_free(ctx, dops);
-    free_csr(ctx, Ht);
-    for (int c = 0; c < n_c; ++c) {
-        free_csr(ctx, Ct[c]);
-        free_csr(ctx, CtC[c]);
-        free_csr(ctx, CtCt[c]);
+    free_ops(ctx, o);
+    return SS_OK;
+}
+
+ss_status batch_lrows(ss_ctx ctx, const DeviceCSR& H, const std::vector<DeviceCSR>& C, const int64_t* row_off_d,
+                      const int64_t* doff_d, int64_t nsys, int64_t P, int32_t reserve_row0, BatchRows& out) {
+    out = BatchRows();
+    const int n_c = (int)C.size();
+    OpPrep o;
+    ss_status st = prep_ops(ctx, H, C, o);
+    if (st != SS_OK) { free_ops(ctx, o); return st; }
+    CsrRef h{H.row_ptr, H.col, H.val}, ht{o.Ht.row_ptr, o.Ht.col, o.Ht.val};
+    int32_t* cnt = nullptr;
+    auto fail = [&](ss_status e) { dev_free(ctx, cnt); free_ops(ctx, o); batch_rows_free(ctx, out); return e; };
+    if ((st = dev_alloc_n(ctx, &cnt, (size_t)P + 1)) != SS_OK) return fail(st);
+    if ((st = dev_alloc_n(ctx, &out.off, (size_t)P + 1)) != SS_OK) return fail(st);
+    if ((st = dev_alloc_n(ctx, &out.cnt, (size_t)P + 1)) != SS_OK) return fail(st);
+    if (P > 0)
+        lrow_count_b<<<(ss_count_launch(), grid_for(P, 256)), 256, 0, ctx->stream>>>(h, ht, o.dops, n_c, row_off_d,
+                                                                                      doff_d, nsys, reserve_row0, cnt);
+    if ((st = exclusive_scan_i32(ctx, cnt, out.off, P, &out.total)) != SS_OK) return fail(st);
+    if ((st = dev_alloc_n(ctx, &out.key, (size_t)out.total)) != SS_OK) return fail(st);
+    if ((st = dev_alloc_n(ctx, &out.val, (size_t)out.total)) != SS_OK) return fail(st);
+    if (P > 0)
+        lrow_build_b<<<(ss_count_launch(), grid_for(P, 128)), 128, 0, ctx->stream>>>(
+            h, ht, o.dops, n_c, row_off_d, doff_d, nsys, out.off, out.key, out.val, out.cnt);
+    cudaError_t e = cudaGetLastError();
+    dev_free(ctx, cnt);
+    cnt = nullptr;
+    free_ops(ctx, o);
+    if (e != cudaSuccess) {
+        batch_rows_free(ctx, out);
+        return cuda_check(ctx, e, "batched Liouvillian rows");
     }
     return SS_OK;
+}
+
+void batch_rows_free(ss_ctx ctx, BatchRows& r) {
+    dev_free(ctx, r.off);
+    dev_free(ctx, r.cnt);
+    dev_free(ctx, r.key);
+    dev_free(ctx, r.val);
+    r = BatchRows();
 }

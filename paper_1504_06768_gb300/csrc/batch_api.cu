@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <string>
+#include <tuple>
 #include <memory>
+#include <new>
 #include <thread>
 #include <vector>
 
@@ -26,25 +29,28 @@ struct PackedDev {                        // device arrays of one packed operand
     int32_t nunits = 0, G = 1, E = 1, nlev = 0;
 };
 
+struct PackedHost {
+    std::vector<int32_t> rows, col, src, ovb, ove, lvl;
+    int32_t nunits = 0, G = 1, E = 1, nlev = 0;
+};
+
 struct Pattern {                          // per distinct pattern of L~ (before ordering)
-    std::vector<int32_t> rp, col;         // natural-order pattern (for exact comparison)
+    std::vector<int32_t> rp, col;         // natural-order pattern
+    int64_t d = 0;
     std::vector<int32_t> perm, iperm, tidx;
     int32_t r0 = 0;
-    int64_t bw = 0, profile = 0;
+    // host products of the analysis (uploaded by upload_pattern)
+    std::vector<int32_t> prp, pcol, map, dpos, lorder, lptr, lunits, uunits;
+    PackedHost hl, hu, ha;
+    ss_status status = SS_OK;
+    std::string error;
     // device arrays of the permuted structure
+    int32_t *prp_d = nullptr, *pcol_d = nullptr, *map_d = nullptr;
     int32_t *perm_d = nullptr, *tidx_d = nullptr, *dpos_d = nullptr;
     int32_t *lo_units = nullptr, *up_units = nullptr, *lvl_ptr = nullptr, *lvl_rows = nullptr;
     int32_t lo_nunits = 0, up_nunits = 0, lo_g = 1, up_g = 1, a_g = 1, n_levels = 0, up_levels = 0;
     PackedDev lo, up, pa;
 };
-
-uint64_t fnv1a(const std::vector<int32_t>& a, uint64_t h) {
-    for (int32_t v : a) {
-        h ^= (uint32_t)v;
-        h *= 1099511628211ull;
-    }
-    return h;
-}
 
 int lanes_for(double avg) {
     int g = 1;
@@ -54,11 +60,6 @@ int lanes_for(double avg) {
 
 // Lane-major packing of one CSR operand (see PackedOp): unit_rows holds R = 32/G
 // row ids per unit; range(i) gives the CSR range [s, e) of row i's entries.
-struct PackedHost {
-    std::vector<int32_t> rows, col, src, ovb, ove, lvl;
-    int32_t nunits = 0, G = 1, E = 1, nlev = 0;
-};
-
 // First unit of each level when each level's rows are cut into units of R.
 std::vector<int32_t> unit_levels(const std::vector<int32_t>& lptr, int R) {
     std::vector<int32_t> lvl(1, 0);
@@ -115,8 +116,12 @@ ss_status upload_vec(ss_ctx ctx, const std::vector<T>& h, T** d) {
     return SS_OK;
 }
 
-ss_status build_pattern(ss_ctx ctx, Pattern& P, const DeviceCSR& A, int64_t d, int use_rcm) {
-    const int64_t n = A.n_rows;
+// Host analysis of one pattern: RCM ordering (section "Direct
+// factorization"), the permuted pattern with the gather map of its values,
+// the level sets of the two triangles and the packed operands.  Runs on any
+// host thread; touches nothing on the device.
+void build_pattern_host(Pattern& P, int use_rcm) {
+    const int64_t n = (int64_t)P.rp.size() - 1, d = P.d;
     P.perm.resize(n);
     if (use_rcm) rcm_host(n, P.rp.data(), P.col.data(), P.perm.data());
     else for (int64_t i = 0; i < n; ++i) P.perm[i] = (int32_t)i;
@@ -125,48 +130,66 @@ ss_status build_pattern(ss_ctx ctx, Pattern& P, const DeviceCSR& A, int64_t d, i
     P.tidx.resize(d);
     for (int64_t i = 0; i < d; ++i) P.tidx[i] = P.iperm[i * (d + 1)];
     P.r0 = P.iperm[0];
-    // permuted pattern on the host (rows gathered, columns relabelled and sorted)
-    std::vector<int32_t> prp(n + 1, 0), pcol(P.col.size());
+    // permuted pattern (rows gathered, columns relabelled and sorted) and the
+    // natural-order position each permuted entry comes from
+    std::vector<int32_t>& prp = P.prp;
+    std::vector<int32_t>& pcol = P.pcol;
+    prp.assign(n + 1, 0);
+    pcol.resize(P.col.size());
+    P.map.resize(P.col.size());
     for (int64_t r = 0; r < n; ++r) prp[r + 1] = prp[r] + (P.rp[P.perm[r] + 1] - P.rp[P.perm[r]]);
-    std::vector<int32_t> dpos(n, -1);
+    P.dpos.assign(n, -1);
+    std::vector<std::pair<int32_t, int32_t>> row;
     for (int64_t r = 0; r < n; ++r) {
-        int32_t o = prp[r], i = P.perm[r];
-        for (int32_t t = P.rp[i]; t < P.rp[i + 1]; ++t) pcol[o++] = P.iperm[P.col[t]];
-        std::sort(pcol.begin() + prp[r], pcol.begin() + prp[r + 1]);
-        for (int32_t t = prp[r]; t < prp[r + 1]; ++t)
-            if (pcol[t] == r) dpos[r] = t;
+        const int32_t i = P.perm[r];
+        row.clear();
+        for (int32_t t = P.rp[i]; t < P.rp[i + 1]; ++t) row.emplace_back(P.iperm[P.col[t]], t);
+        std::sort(row.begin(), row.end());
+        int32_t o = prp[r];
+        for (const auto& e : row) {
+            if (e.first == r) P.dpos[r] = o;
+            pcol[o] = e.first;
+            P.map[o] = e.second;
+            ++o;
+        }
     }
     int64_t lo = 0, up = 0;
-    P.bw = 0;
     for (int64_t r = 0; r < n; ++r) {
-        if (dpos[r] < 0) return set_error(ctx, SS_ZERO_PIVOT, "iLU(0): missing diagonal entry in row " + std::to_string(r));
-        lo += dpos[r] - prp[r];
-        up += prp[r + 1] - dpos[r] - 1;
+        if (P.dpos[r] < 0) {
+            P.status = SS_ZERO_PIVOT;
+            P.error = "iLU(0): missing diagonal entry in row " + std::to_string(r);
+            return;
+        }
+        lo += P.dpos[r] - prp[r];
+        up += prp[r + 1] - P.dpos[r] - 1;
     }
-    std::vector<int32_t> lorder, lptr, uorder, uptr, lunits, uunits;
-    P.n_levels = level_sets_host(n, prp.data(), pcol.data(), true, lorder, lptr);
+    std::vector<int32_t> uorder, uptr;
+    P.n_levels = level_sets_host(n, prp.data(), pcol.data(), true, P.lorder, P.lptr);
     P.up_levels = level_sets_host(n, prp.data(), pcol.data(), false, uorder, uptr);
     P.lo_g = lanes_for(n ? (double)lo / n : 1.0);
     P.up_g = lanes_for(n ? (double)up / n : 1.0);
     P.a_g = lanes_for(n ? (double)P.col.size() / n : 1.0);
-    level_units_host(lorder, lptr, 32 / P.lo_g, lunits);
-    level_units_host(uorder, uptr, 32 / P.up_g, uunits);
-    P.lo_nunits = (int32_t)(lunits.size() / (32 / P.lo_g));
-    P.up_nunits = (int32_t)(uunits.size() / (32 / P.up_g));
+    level_units_host(P.lorder, P.lptr, 32 / P.lo_g, P.lunits);
+    level_units_host(uorder, uptr, 32 / P.up_g, P.uunits);
+    P.lo_nunits = (int32_t)(P.lunits.size() / (32 / P.lo_g));
+    P.up_nunits = (int32_t)(P.uunits.size() / (32 / P.up_g));
     // packed operands: the two triangles (level-aligned units) and A (consecutive rows)
-    PackedHost hl, hu, ha;
-    pack_host(lunits, P.lo_g, pcol, [&](int32_t i) { return std::make_pair(prp[i], dpos[i]); }, hl);
-    pack_host(uunits, P.up_g, pcol, [&](int32_t i) { return std::make_pair(dpos[i] + 1, prp[i + 1]); }, hu);
-    hl.lvl = unit_levels(lptr, 32 / P.lo_g);
-    hu.lvl = unit_levels(uptr, 32 / P.up_g);
-    hl.nlev = (int32_t)hl.lvl.size() - 1;
-    hu.nlev = (int32_t)hu.lvl.size() - 1;
+    const std::vector<int32_t>& dpos = P.dpos;
+    pack_host(P.lunits, P.lo_g, pcol, [&](int32_t i) { return std::make_pair(prp[i], dpos[i]); }, P.hl);
+    pack_host(P.uunits, P.up_g, pcol, [&](int32_t i) { return std::make_pair(dpos[i] + 1, prp[i + 1]); }, P.hu);
+    P.hl.lvl = unit_levels(P.lptr, 32 / P.lo_g);
+    P.hu.lvl = unit_levels(uptr, 32 / P.up_g);
+    P.hl.nlev = (int32_t)P.hl.lvl.size() - 1;
+    P.hu.nlev = (int32_t)P.hu.lvl.size() - 1;
     {
         const int R = 32 / P.a_g;
         std::vector<int32_t> arows(((n + R - 1) / R) * R, -1);
         for (int64_t i = 0; i < n; ++i) arows[i] = (int32_t)i;
-        pack_host(arows, P.a_g, pcol, [&](int32_t i) { return std::make_pair(prp[i], prp[i + 1]); }, ha);
+        pack_host(arows, P.a_g, pcol, [&](int32_t i) { return std::make_pair(prp[i], prp[i + 1]); }, P.ha);
     }
+}
+
+ss_status upload_pattern(ss_ctx ctx, Pattern& P) {
     auto up_packed = [&](PackedHost& h, PackedDev& dv) -> ss_status {
         dv.nunits = h.nunits;
         dv.G = h.G;
@@ -180,16 +203,19 @@ ss_status build_pattern(ss_ctx ctx, Pattern& P, const DeviceCSR& A, int64_t d, i
         if (h.nlev > 0) SS_TRY(upload_vec(ctx, h.lvl, &dv.lvl));
         return SS_OK;
     };
-    SS_TRY(up_packed(hl, P.lo));
-    SS_TRY(up_packed(hu, P.up));
-    SS_TRY(up_packed(ha, P.pa));
+    SS_TRY(up_packed(P.hl, P.lo));
+    SS_TRY(up_packed(P.hu, P.up));
+    SS_TRY(up_packed(P.ha, P.pa));
+    SS_TRY(upload_vec(ctx, P.prp, &P.prp_d));
+    SS_TRY(upload_vec(ctx, P.pcol, &P.pcol_d));
+    SS_TRY(upload_vec(ctx, P.map, &P.map_d));
     SS_TRY(upload_vec(ctx, P.perm, &P.perm_d));
     SS_TRY(upload_vec(ctx, P.tidx, &P.tidx_d));
-    SS_TRY(upload_vec(ctx, dpos, &P.dpos_d));
-    SS_TRY(upload_vec(ctx, lunits, &P.lo_units));
-    SS_TRY(upload_vec(ctx, uunits, &P.up_units));
-    SS_TRY(upload_vec(ctx, lptr, &P.lvl_ptr));
-    SS_TRY(upload_vec(ctx, lorder, &P.lvl_rows));
+    SS_TRY(upload_vec(ctx, P.dpos, &P.dpos_d));
+    SS_TRY(upload_vec(ctx, P.lunits, &P.lo_units));
+    SS_TRY(upload_vec(ctx, P.uunits, &P.up_units));
+    SS_TRY(upload_vec(ctx, P.lptr, &P.lvl_ptr));
+    SS_TRY(upload_vec(ctx, P.lorder, &P.lvl_rows));
     return SS_OK;
 }
 
@@ -206,6 +232,9 @@ void free_pattern(ss_ctx ctx, Pattern& P) {
     free_packed(ctx, P.lo);
     free_packed(ctx, P.up);
     free_packed(ctx, P.pa);
+    dev_free(ctx, P.prp_d);
+    dev_free(ctx, P.pcol_d);
+    dev_free(ctx, P.map_d);
     dev_free(ctx, P.perm_d);
     dev_free(ctx, P.tidx_d);
     dev_free(ctx, P.dpos_d);
@@ -253,139 +282,101 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
     if (fastidx.empty()) return worst;
 
     // ------------------------------------------------------------ setup
-    struct Sys {
-        ss_mat L = nullptr, A = nullptr;
-        DeviceCSR Ap;
-        int pat = -1;
-        double w = 0.0;
-    };
-    std::vector<Sys> sys(fastidx.size());
+    // (1) every system's L~ with a fixed number of launches; (2) systems that
+    // share a pattern (hash, then an exact check on the device) share one RCM
+    // ordering, level schedule and packing, analysed on host threads, one per
+    // distinct pattern; (3) one gather puts every system's values in its
+    // pattern's order.
+    const size_t ns = fastidx.size();
+    std::vector<const ss_csr_view*> Hv(ns), Cv(ns);
+    std::vector<int> ncv(ns);
+    for (size_t q = 0; q < ns; ++q) {
+        const int k = fastidx[q];
+        Hv[q] = &H[k];
+        ncv[q] = n_c[k];
+        Cv[q] = n_c[k] ? c_ops[k] : nullptr;
+    }
+    BatchLt blt;
     std::vector<std::unique_ptr<Pattern>> pats;
-    std::map<uint64_t, std::vector<int>> by_hash;
     std::vector<void*> owned;
     auto cleanup = [&]() {
-        for (auto& s : sys) {
-            if (s.L) ss_mat_free(s.L);
-            if (s.A) ss_mat_free(s.A);
-            free_csr(ctx, s.Ap);
-        }
+        batch_lt_free(ctx, blt);
         for (auto& p : pats) free_pattern(ctx, *p);
         for (void* p : owned) dev_free(ctx, p);
         cudaStreamSynchronize(ctx->stream);
     };
 #define BSTEP(call) do { ss_status _st = (call); if (_st != SS_OK) { cleanup(); return _st; } } while (0)
-    // Setup runs on worker threads, each with its own stream: (A) assembly,
-    // trace row and the pattern of L~; (B, serial) one RCM ordering and level
-    // schedule per distinct pattern; (C) the symmetric permutations.
-    const size_t ns = fastidx.size();
-    const int nthreads = (int)std::max<size_t>(
-        1, std::min<size_t>(ns, std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()))));
-    std::vector<ss_ctx_s> wctx(nthreads);
-    for (auto& w : wctx) {
-        w.device = ctx->device;
-        w.num_sms = ctx->num_sms;
-        SS_CUDA(ctx, cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking));
+    BSTEP(batch_trace_systems(ctx, Hv, ncv, Cv, opt.w, blt));
+    std::vector<int> pat_of(ns, -1), rep_sys;
+    {
+        std::map<std::tuple<int64_t, int64_t, int64_t, unsigned long long>, int> first;
+        std::vector<std::pair<int, int>> pairs;
+        for (size_t q = 0; q < ns; ++q) {
+            auto key = std::make_tuple(blt.d[q], blt.n[q], blt.meta[q].nnz, blt.meta[q].hash);
+            auto it = first.find(key);
+            if (it == first.end()) {
+                first.emplace(key, (int)rep_sys.size());
+                pat_of[q] = (int)rep_sys.size();
+                rep_sys.push_back((int)q);
+            } else {
+                pat_of[q] = it->second;
+                pairs.emplace_back((int)q, rep_sys[it->second]);
+            }
+        }
+        std::vector<int> mismatch;
+        BSTEP(batch_verify_patterns(ctx, blt, pairs, mismatch));
+        for (size_t k = 0; k < pairs.size(); ++k)
+            if (mismatch[k]) {                 // equal hashes, different patterns: a pattern of its own
+                pat_of[pairs[k].first] = (int)rep_sys.size();
+                rep_sys.push_back(pairs[k].first);
+            }
     }
-    auto drop_streams = [&]() {
-        for (auto& w : wctx) {
-            cudaStreamSynchronize(w.stream);
-            cudaStreamDestroy(w.stream);
+    for (size_t p = 0; p < rep_sys.size(); ++p) {
+        pats.emplace_back(new Pattern());
+        pats.back()->d = blt.d[rep_sys[p]];
+        BSTEP(batch_download_pattern(ctx, blt, rep_sys[p], pats.back()->rp, pats.back()->col));
+    }
+    SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    {
+        const size_t np = pats.size();
+        const size_t nth = std::max<size_t>(1, std::min<size_t>(np, std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()))));
+        if (nth <= 1) {
+            for (auto& P : pats) build_pattern_host(*P, opt.use_rcm);
+        } else {
+            std::vector<std::thread> th;
+            for (size_t t = 0; t < nth; ++t)
+                th.emplace_back([&, t]() {
+                    for (size_t p = t; p < np; p += nth) build_pattern_host(*pats[p], opt.use_rcm);
+                });
+            for (auto& x : th) x.join();
         }
-    };
-    std::vector<std::vector<int32_t>> prps(ns), pcols(ns);
-    std::vector<ss_status> wst(ns, SS_OK);
-    std::vector<std::string> werr(ns);
-    std::vector<int64_t> dims(ns, 0);
-    auto run_workers = [&](auto&& body) {
-        std::vector<std::thread> th;
-        for (int t = 0; t < nthreads; ++t)
-            th.emplace_back([&, t]() {
-                cudaSetDevice(ctx->device);
-                for (size_t q = t; q < ns; q += nthreads) body(&wctx[t], q);
-                cudaStreamSynchronize(wctx[t].stream);
-            });
-        for (auto& x : th) x.join();
-        for (size_t q = 0; q < ns; ++q)
-            if (wst[q] != SS_OK) return (ss_status)set_error(ctx, wst[q], werr[q]);
-        return SS_OK;
-    };
-    ss_status pst = run_workers([&](ss_ctx wc, size_t q) {
-        const int k = fastidx[q];
-        ss_status st = assemble_liouvillian(wc, &H[k], n_c[k], n_c[k] ? c_ops[k] : nullptr, &sys[q].L);
-        if (st == SS_OK) st = add_trace_row(wc, sys[q].L, opt.w, &sys[q].A, &sys[q].w);
-        if (st == SS_OK) {
-            const DeviceCSR& A = sys[q].A->m;
-            dims[q] = sys[q].L->d;
-            prps[q].resize(A.n_rows + 1);
-            pcols[q].resize(A.nnz);
-            cudaMemcpyAsync(prps[q].data(), A.row_ptr, sizeof(int32_t) * prps[q].size(), cudaMemcpyDeviceToHost,
-                            wc->stream);
-            cudaMemcpyAsync(pcols[q].data(), A.col, sizeof(int32_t) * pcols[q].size(), cudaMemcpyDeviceToHost,
-                            wc->stream);
-            cudaError_t e = cudaStreamSynchronize(wc->stream);
-            if (e != cudaSuccess) st = cuda_check(wc, e, "pattern download");
-        }
-        if (sys[q].L) {
-            ss_mat_free(sys[q].L);
-            sys[q].L = nullptr;
-        }
-        wst[q] = st;
-        if (st != SS_OK) werr[q] = wc->last_error;
-    });
-    if (pst != SS_OK) { drop_streams(); cleanup(); return pst; }
+    }
+    for (auto& P : pats) {
+        if (P->status != SS_OK) { ss_status e = set_error(ctx, P->status, P->error); cleanup(); return e; }
+        BSTEP(upload_pattern(ctx, *P));
+    }
     int max_n = 0;
-    for (size_t q = 0; q < ns; ++q) {
-        const uint64_t h = fnv1a(pcols[q], fnv1a(prps[q], 1469598103934665603ull));
-        int found = -1;
-        for (int pi : by_hash[h])
-            if (pats[pi]->rp == prps[q] && pats[pi]->col == pcols[q]) { found = pi; break; }
-        if (found < 0) {
-            pats.emplace_back(new Pattern());
-            Pattern& P = *pats.back();
-            P.rp.swap(prps[q]);
-            P.col.swap(pcols[q]);
-            ss_status st = build_pattern(ctx, P, sys[q].A->m, dims[q], opt.use_rcm);
-            if (st != SS_OK) { drop_streams(); cleanup(); return st; }
-            found = (int)pats.size() - 1;
-            by_hash[h].push_back(found);
-        }
-        sys[q].pat = found;
-        max_n = std::max<int>(max_n, (int)sys[q].A->m.n_rows);
-    }
-    pst = run_workers([&](ss_ctx wc, size_t q) {
-        wst[q] = permute_impl(wc, sys[q].A->m, pats[sys[q].pat]->perm.data(), sys[q].Ap);
-        if (wst[q] != SS_OK) werr[q] = wc->last_error;
-    });
-    drop_streams();
-    if (pst != SS_OK) { cleanup(); return pst; }
-    // per-system buffers and descriptors
-    std::vector<BatchSys> hs(fastidx.size());
-    for (size_t q = 0; q < fastidx.size(); ++q) {
-        const Pattern& P = *pats[sys[q].pat];
-        const DeviceCSR& Ap = sys[q].Ap;
-        const int64_t n = Ap.n_rows, nnz = Ap.nnz;
-        BatchSys& b = hs[q];
+    for (size_t q = 0; q < ns; ++q) max_n = std::max<int>(max_n, (int)blt.n[q]);
+    // per-system buffers (one allocation) and descriptors; describe() lays
+    // out system q's buffers from address base and returns the bytes used
+    const size_t inner = mixed ? sizeof(float2) : sizeof(double2);
+    auto describe = [&](size_t q, uintptr_t base, BatchSys& b, GatherEntry& g) -> size_t {
+        const Pattern& P = *pats[pat_of[q]];
+        const int64_t n = blt.n[q], nnz = blt.meta[q].nnz;
+        size_t off = 0;
+        auto take = [&](size_t sz) { uintptr_t p = base + off; off += (sz + 255) & ~size_t(255); return p; };
         std::memset(&b, 0, sizeof(b));
+        double2* aval = reinterpret_cast<double2*>(take(nnz * sizeof(double2)));
+        g = GatherEntry{P.map_d, aval, blt.meta[q].nz_off, nnz};
         b.n = (int32_t)n;
-        b.d = (int32_t)sys[q].A->d;
-        b.a_rp = Ap.row_ptr;
-        b.a_col = Ap.col;
-        b.a_val = Ap.val;
-        b.f_rp = Ap.row_ptr;
-        b.f_col = Ap.col;
+        b.d = (int32_t)blt.d[q];
+        b.a_rp = P.prp_d;
+        b.a_col = P.pcol_d;
+        b.a_val = aval;
+        b.f_rp = P.prp_d;
+        b.f_col = P.pcol_d;
         b.f_dpos = P.dpos_d;
         b.factor_on_device = 1;
-        const size_t inner = mixed ? sizeof(float2) : sizeof(double2);
-        char* blk = nullptr;
-        const size_t pk_slots = ((size_t)P.lo.nunits * P.lo.E + (size_t)P.up.nunits * P.up.E +
-                                 (size_t)P.pa.nunits * P.pa.E) * 32;
-        const size_t bytes = nnz * sizeof(double2) + n * sizeof(double2) + (mixed ? 2 * nnz * sizeof(float2) + n * sizeof(float2) : 0) +
-                             10 * n * inner + 2 * n * sizeof(double2) + (rho_on_device ? 0 : n * sizeof(double2)) +
-                             pk_slots * inner + 8 * 256;
-        BSTEP(dev_alloc(ctx, reinterpret_cast<void**>(&blk), bytes));
-        owned.push_back(blk);
-        size_t off = 0;
-        auto take = [&](size_t sz) { char* p = blk + off; off += (sz + 15) & ~size_t(15); return p; };
         b.f_val = reinterpret_cast<double2*>(take(nnz * sizeof(double2)));
         b.f_inv = reinterpret_cast<double2*>(take(n * sizeof(double2)));
         if (mixed) {
@@ -393,7 +384,7 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
             b.a_val32 = reinterpret_cast<float2*>(take(nnz * sizeof(float2)));
             b.f_inv32 = reinterpret_cast<float2*>(take(n * sizeof(float2)));
         }
-        b.work = take(10 * n * inner);
+        b.work = reinterpret_cast<void*>(take(10 * n * inner));
         b.x64 = reinterpret_cast<double2*>(take(n * sizeof(double2)));
         b.r64 = reinterpret_cast<double2*>(take(n * sizeof(double2)));
         b.rho_out = rho_on_device ? reinterpret_cast<double2*>(rho_out[fastidx[q]])
@@ -409,7 +400,7 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
             o.E = dv.E;
             o.lvl = dv.lvl;
             o.nlev = dv.nlev;
-            o.val = take((size_t)dv.nunits * dv.E * 32 * inner);
+            o.val = reinterpret_cast<void*>(take((size_t)dv.nunits * dv.E * 32 * inner));
         };
         set_op(b.lo, P.lo);
         set_op(b.up, P.up);
@@ -418,11 +409,21 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
         b.lvl_rows = P.lvl_rows;
         b.n_levels = P.n_levels;
         b.r0 = P.r0;
-        b.w = sys[q].w;
+        b.w = blt.w[q];
         b.sigma = 0.0;
         b.perm = P.perm_d;
         b.tidx = P.tidx_d;
-    }
+        return off;
+    };
+    std::vector<BatchSys> hs(ns);
+    std::vector<GatherEntry> gather(ns);
+    std::vector<size_t> boff(ns + 1, 0);
+    for (size_t q = 0; q < ns; ++q) boff[q + 1] = boff[q] + describe(q, 0, hs[q], gather[q]);
+    char* blk_all = nullptr;
+    BSTEP(dev_alloc(ctx, reinterpret_cast<void**>(&blk_all), boff[ns]));
+    owned.push_back(blk_all);
+    for (size_t q = 0; q < ns; ++q) describe(q, reinterpret_cast<uintptr_t>(blk_all) + boff[q], hs[q], gather[q]);
+    BSTEP(batch_gather_values(ctx, blt, gather));
     BatchSys* dsys = nullptr;
     int* ctl = nullptr;
     BSTEP(dev_alloc_n(ctx, &dsys, hs.size()));
@@ -454,7 +455,7 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
     const double t2 = now_ms();
     for (size_t q = 0; q < fastidx.size(); ++q) {
         const int k = fastidx[q];
-        const Pattern& P = *pats[sys[q].pat];
+        const Pattern& P = *pats[pat_of[q]];
         if (herr) hs[q].status = SS_ERR_TIMEOUT;
         if (infos) {
             ss_info& inf = infos[k];
@@ -463,10 +464,10 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
             inf.iters = hs[q].iters;
             inf.outer_iters = hs[q].outer;
             inf.resid_Lrho = hs[q].resid;
-            inf.w_used = sys[q].w;
+            inf.w_used = blt.w[q];
             inf.n = hs[q].n;
-            inf.nnz = sys[q].Ap.nnz;
-            inf.nnz_factors = sys[q].Ap.nnz;
+            inf.nnz = blt.meta[q].nnz;
+            inf.nnz_factors = blt.meta[q].nnz;
             inf.levels_lower = P.n_levels;
             inf.levels_upper = P.up_levels;
             inf.ms_setup = (t1 - t0) / fastidx.size();
@@ -481,4 +482,67 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
 #undef BSTEP
     if (worst != SS_OK) ctx->last_error = "at least one system did not converge (see infos)";
     return worst;
+}
+
+extern "C" ss_status assemble_trace_batched(ss_ctx ctx, int n_sys, const ss_csr_view* H, const int* n_c,
+                                            const ss_csr_view* const* c_ops, double w, ss_mat* out,
+                                            double* w_used) {
+    if (!ctx) return SS_ERR_INVALID;
+    SS_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (n_sys < 0 || (n_sys > 0 && (!H || !n_c || !out))) return set_error(ctx, SS_ERR_INVALID, "null argument");
+    for (int k = 0; k < n_sys; ++k) out[k] = nullptr;
+    if (n_sys == 0) return SS_OK;
+    std::vector<const ss_csr_view*> Hv(n_sys), Cv(n_sys);
+    std::vector<int> ncv(n_sys);
+    for (int k = 0; k < n_sys; ++k) {
+        Hv[k] = &H[k];
+        ncv[k] = n_c[k];
+        Cv[k] = n_c[k] ? (c_ops ? c_ops[k] : nullptr) : nullptr;
+    }
+    BatchLt blt;
+    SS_TRY(batch_trace_systems(ctx, Hv, ncv, Cv, w, blt));
+    ss_status st = SS_OK;
+    for (int k = 0; k < n_sys && st == SS_OK; ++k) {
+        DeviceCSR m;
+        m.n_rows = m.n_cols = blt.n[k];
+        m.nnz = blt.meta[k].nnz;
+        st = dev_alloc_n(ctx, &m.row_ptr, (size_t)m.n_rows + 1);
+        if (st == SS_OK) st = dev_alloc_n(ctx, &m.col, (size_t)m.nnz);
+        if (st == SS_OK) st = dev_alloc_n(ctx, &m.val, (size_t)m.nnz);
+        cudaError_t e = cudaSuccess;
+        if (st == SS_OK)
+            e = cudaMemcpyAsync(m.row_ptr, blt.rp + blt.row_off[k] + k, sizeof(int32_t) * (m.n_rows + 1),
+                                cudaMemcpyDeviceToDevice, ctx->stream);
+        if (st == SS_OK && e == cudaSuccess && m.nnz > 0)
+            e = cudaMemcpyAsync(m.col, blt.col + blt.meta[k].nz_off, sizeof(int32_t) * m.nnz, cudaMemcpyDeviceToDevice,
+                                ctx->stream);
+        if (st == SS_OK && e == cudaSuccess && m.nnz > 0)
+            e = cudaMemcpyAsync(m.val, blt.val + blt.meta[k].nz_off, sizeof(double2) * m.nnz,
+                                cudaMemcpyDeviceToDevice, ctx->stream);
+        if (st == SS_OK && e != cudaSuccess) st = cuda_check(ctx, e, "assemble_trace_batched");
+        ss_mat h = nullptr;
+        if (st == SS_OK) {
+            h = new (std::nothrow) ss_mat_s();
+            if (!h) st = set_error(ctx, SS_ERR_OOM, "host allocation failed");
+        }
+        if (st != SS_OK) {
+            free_csr(ctx, m);
+            break;
+        }
+        h->m = m;
+        h->d = blt.d[k];
+        out[k] = h;
+    }
+    if (w_used && st == SS_OK)
+        for (int k = 0; k < n_sys; ++k) w_used[k] = blt.w[k];
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    batch_lt_free(ctx, blt);
+    if (st == SS_OK && e != cudaSuccess) st = cuda_check(ctx, e, "assemble_trace_batched");
+    if (st != SS_OK)
+        for (int k = 0; k < n_sys; ++k)
+            if (out[k]) {
+                ss_mat_free(out[k]);
+                out[k] = nullptr;
+            }
+    return st;
 }

@@ -4,6 +4,9 @@
 // finalisation without leaving the kernel.
 #pragma once
 
+#include <utility>
+#include <vector>
+
 #include "common.cuh"
 
 constexpr int BATCH_THREADS = 512;
@@ -71,6 +74,50 @@ struct BatchParams {
     int power;                  // inverse power (FP64 only)
     uint64_t seed;
 };
+
+// ------------------------------------------------------- batched setup
+
+struct BatchMeta {                  // per system, from the device
+    int64_t nz_off, nnz;            // entries of the system in BatchLt::col / val
+    unsigned long long hash;        // hash of the pattern (equal patterns, equal hashes)
+};
+
+// Trace-row systems L~ = L + wT (Eq. linear) of a batch, concatenated on the
+// device: system s has n[s] = d[s]^2 rows, local row pointers at
+// rp[row_off[s] + s ...] (n[s] + 1 entries, starting at 0), local columns and
+// values at col / val[meta[s].nz_off ...].
+struct BatchLt {
+    int64_t ns = 0;
+    std::vector<int64_t> d, n, row_off;
+    std::vector<BatchMeta> meta;
+    std::vector<double> w;
+    int32_t* rp = nullptr;
+    int32_t* col = nullptr;
+    double2* val = nullptr;
+    int64_t* row_off_d = nullptr;
+    BatchMeta* meta_d = nullptr;
+};
+
+struct GatherEntry {                // dst[k] = val[src_off + map[k]], k < nnz
+    const int32_t* map;
+    double2* dst;
+    int64_t src_off, nnz;
+};
+
+// Assembly (Eq. lindblad), weight w (w_in > 0: as given, else mean |L_ii|) and
+// trace row of every system, with a number of launches that does not grow
+// with the number of systems.  Each system's L~ is entry for entry the one
+// assemble_liouvillian + add_trace_row give.
+ss_status batch_trace_systems(ss_ctx ctx, const std::vector<const ss_csr_view*>& H, const std::vector<int>& n_c,
+                              const std::vector<const ss_csr_view*>& C, double w_in, BatchLt& out);
+void batch_lt_free(ss_ctx ctx, BatchLt& b);
+// mismatch[k] = 1 when the patterns of systems pairs[k] differ (same n, nnz).
+ss_status batch_verify_patterns(ss_ctx ctx, const BatchLt& b, const std::vector<std::pair<int, int>>& pairs,
+                                std::vector<int>& mismatch);
+// Asynchronous copy of system s's pattern to the host (synchronise the stream before use).
+ss_status batch_download_pattern(ss_ctx ctx, const BatchLt& b, int s, std::vector<int32_t>& rp,
+                                 std::vector<int32_t>& col);
+ss_status batch_gather_values(ss_ctx ctx, const BatchLt& b, const std::vector<GatherEntry>& tab);
 
 size_t batch_smem_bytes(int n, bool mixed);
 int batch_max_n(bool mixed);

@@ -152,11 +152,33 @@ void free_csr(ss_ctx ctx, DeviceCSR& m);
 ss_status exclusive_scan_i32(ss_ctx ctx, const int32_t* counts, int32_t* out, int64_t n, int64_t* total);
 // Position of the diagonal entry in each row (-1 when absent).
 ss_status find_diag(ss_ctx ctx, const DeviceCSR& m, int32_t* diag_pos);
+// Sizes and pointers of a CSR view; a host view's contents too (row pointers
+// spanning nnz, sorted unique in-range columns, finite values).
+ss_status check_csr_view(ss_ctx ctx, const ss_csr_view* v);
 ss_status upload_csr(ss_ctx ctx, const ss_csr_view* v, DeviceCSR& out);
 
 // ----------------------------------------------------------- kernels API
 
 ss_status assemble_impl(ss_ctx ctx, const DeviceCSR& H, const std::vector<DeviceCSR>& C, DeviceCSR& L);
+
+// Liouvillian rows of a batch of systems whose operators are stacked
+// block-diagonally (H and each C_k of all systems, an absent operator being
+// an empty block).  System s owns operator rows [doff[s], doff[s+1]) and rows
+// [row_off[s], row_off[s+1]) of the concatenated Liouvillians (device arrays
+// of nsys + 1 entries, P = row_off[nsys]).  Row p's stored entries are
+// key[off[p] .. off[p] + cnt[p]) (key = local column) and val at the same
+// positions; each system's row 0 has reserve_row0 ? d : 0 spare slots after
+// its candidates.  The arithmetic of every entry is that of assemble_impl.
+struct BatchRows {
+    int32_t* off = nullptr;               // P + 1 candidate offsets
+    int32_t* cnt = nullptr;               // P stored counts
+    unsigned long long* key = nullptr;
+    double2* val = nullptr;
+    int64_t total = 0;                    // candidate slots
+};
+ss_status batch_lrows(ss_ctx ctx, const DeviceCSR& H, const std::vector<DeviceCSR>& C, const int64_t* row_off_d,
+                      const int64_t* doff_d, int64_t nsys, int64_t P, int32_t reserve_row0, BatchRows& out);
+void batch_rows_free(ss_ctx ctx, BatchRows& r);
 ss_status add_trace_row_impl(ss_ctx ctx, const DeviceCSR& L, int64_t d, double w, DeviceCSR& out);
 ss_status mean_abs_diag(ss_ctx ctx, const DeviceCSR& L, double* w);
 ss_status add_shift_impl(ss_ctx ctx, const DeviceCSR& L, double sigma, DeviceCSR& out);

@@ -151,15 +151,12 @@ ss_status find_diag(ss_ctx ctx, const DeviceCSR& m, int32_t* diag_pos) {
     return SS_OK;
 }
 
-// Validate and copy a CSR view into library-owned device memory.
-ss_status upload_csr(ss_ctx ctx, const ss_csr_view* v, DeviceCSR& out) {
-    out = DeviceCSR();
+ss_status check_csr_view(ss_ctx ctx, const ss_csr_view* v) {
     if (!v) return set_error(ctx, SS_ERR_INVALID, "null CSR view");
     if (v->n_rows < 0 || v->n_cols < 0 || v->nnz < 0 || v->nnz > INT32_MAX)
         return set_error(ctx, SS_ERR_INVALID, "bad CSR sizes");
     if (!v->row_ptr || (v->nnz > 0 && (!v->col || !v->val)))
         return set_error(ctx, SS_ERR_INVALID, "null CSR array");
-    cudaMemcpyKind kind = v->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (!v->on_device) {   // host views can be checked cheaply
         if (v->row_ptr[0] != 0 || v->row_ptr[v->n_rows] != v->nnz)
             return set_error(ctx, SS_ERR_INVALID, "row_ptr does not span nnz");
@@ -177,6 +174,14 @@ ss_status upload_csr(ss_ctx ctx, const ss_csr_view* v, DeviceCSR& out) {
             if (!(v->val[t] == v->val[t]) || v->val[t] - v->val[t] != 0.0)
                 return set_error(ctx, SS_ERR_INVALID, "non-finite value in CSR view");
     }
+    return SS_OK;
+}
+
+// Validate and copy a CSR view into library-owned device memory.
+ss_status upload_csr(ss_ctx ctx, const ss_csr_view* v, DeviceCSR& out) {
+    out = DeviceCSR();
+    SS_TRY(check_csr_view(ctx, v));
+    cudaMemcpyKind kind = v->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     out.n_rows = v->n_rows;
     out.n_cols = v->n_cols;
     out.nnz = v->nnz;

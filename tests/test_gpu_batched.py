@@ -83,3 +83,65 @@ def test_batched_falls_back_for_other_methods(ss):
     for s, rho, info in zip(systems, rhos, infos):
         assert info["status"] == 0
         assert trace_distance(rho, steady_state_dense(s.H, s.c_ops)) <= 1e-10
+
+
+def _device_view(m):
+    import scipy.sparse as sp
+    import torch
+    m = sp.csr_matrix(m)
+    m.sort_indices()
+    return (torch.as_tensor(m.indptr.astype(np.int32), device="cuda"),
+            torch.as_tensor(m.indices.astype(np.int32), device="cuda"),
+            torch.as_tensor(m.data.astype(np.complex128), device="cuda"), m.shape[1])
+
+
+def test_assemble_trace_batched_equals_single_calls(ss):
+    """The batched assembly (block-diagonal operator stacks, one launch per
+    stage) gives, entry for entry, the matrix of assemble_liouvillian +
+    add_trace_row for every system, with host and device views, uneven sizes
+    and different numbers of collapse operators."""
+    systems = _mix() + [driven_cavity(N=5, n_th=0.0)]
+    batch = []
+    for k, s in enumerate(systems):
+        if k % 2:
+            batch.append((_device_view(s.H), [_device_view(c) for c in s.c_ops]))
+        else:
+            batch.append((s.H, s.c_ops))
+    out = ss.assemble_trace_batched(batch)
+    for s, (Lt, w) in zip(systems, out):
+        ref, w_ref = ss.add_trace_row(ss.assemble_liouvillian(s.H, s.c_ops))
+        assert w == w_ref, s.name
+        a, b = Lt.to_scipy(), ref.to_scipy()
+        assert a.shape == b.shape and a.nnz == b.nnz, s.name
+        assert np.array_equal(a.indptr, b.indptr) and np.array_equal(a.indices, b.indices), s.name
+        assert np.array_equal(a.data, b.data), s.name
+    # a given weight is used as it is
+    out2 = ss.assemble_trace_batched([(systems[0].H, systems[0].c_ops)], w=2.5)
+    ref2, _ = ss.add_trace_row(ss.assemble_liouvillian(systems[0].H, systems[0].c_ops), 2.5)
+    assert out2[0][1] == 2.5
+    assert np.array_equal(out2[0][0].to_scipy().toarray(), ref2.to_scipy().toarray())
+
+
+def test_batched_device_and_host_views_agree(ss):
+    """steady_state_batched through device views gives the same rho as through
+    host views (the bench's two legs)."""
+    import ctypes as C
+    import torch
+    from paper_1504_06768_gb300 import _binding as B
+    systems = [jaynes_cummings_rwa(seed=s, N=10) for s in range(3)] + [driven_cavity(n_th=0.2)]
+    host, _ = ss.steady_state_batched([(s.H, s.c_ops) for s in systems], tol=1e-10, precision="mixed")
+    ctx = ss.get_context()
+    keep = []
+    Hs = (B.CsrView * len(systems))(*[ss._view(_device_view(s.H), keep) for s in systems])
+    carrs = [(B.CsrView * len(s.c_ops))(*[ss._view(_device_view(c), keep) for c in s.c_ops]) for s in systems]
+    cptrs = (C.POINTER(B.CsrView) * len(systems))(*[C.cast(a, C.POINTER(B.CsrView)) for a in carrs])
+    ncs = (C.c_int * len(systems))(*[len(s.c_ops) for s in systems])
+    rho = [torch.empty(s.d * s.d, dtype=torch.complex128, device="cuda") for s in systems]
+    outs = (C.c_void_p * len(systems))(*[r.data_ptr() for r in rho])
+    infos = (B.Info * len(systems))()
+    opt = ss._options("iterative-bicgstab", 1e-10, "ilu0", "mixed", 1000, 30, 1e-4, 10.0, 0.0, 1e-15, True, 0, 1e-5)
+    st = B.load().steady_state_batched(ctx.handle, len(systems), Hs, ncs, cptrs, C.byref(opt), outs, 1, infos)
+    torch.cuda.synchronize()
+    assert st == 0, B.load().ss_last_error(ctx.handle).decode()
+    for s, r, h in zip(systems, rho, host):
+        assert np.array_equal(r.cpu().numpy().reshape((s.d, s.d), order="F"), h)
