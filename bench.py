@@ -305,12 +305,19 @@ def run_gpu(args):
                 "bytes_model": "per system-iteration: 2 SpMV + 2 M^-1 (matrix and factors once each) + "
                                "30.5 vector passes of n; x iterations summed over the step's systems",
                 "kernel_share_of_step": {k: prof[k][1] / total_ms for k in prof if prof[k][0]}}
-    # traffic per launch from the committed ncu summary, when it matches this build
+    # DRAM traffic per launch from the committed ncu capture, only while the
+    # kernel's source is the one that was profiled and the workload matches
     tr_file = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tr_file):
+        import hashlib
         tr = json.load(open(tr_file))
-        if tr.get("kernel") == dom and tr.get("workload") == "jc40" and tr.get("precision") == args.precision:
+        h = hashlib.sha256()
+        for f in ("batched.cu", "batched.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_1504_06768_gb300", "csrc", f), "rb").read())
+        if (tr.get("kernel") == dom and tr.get("workload") == "jc40" and tr.get("precision") == args.precision
+                and tr.get("batch") == BATCH and tr.get("source_sha256") == h.hexdigest()):
             roofline["traffic"] = tr.get("bytes_per_launch")
+            roofline["traffic_source"] = "profiles/" + tr.get("summary", "traffic.json")
 
     launches_per_step = sum(prof[k][0] for k in prof) / args.steps
     resid = max(i["resid_Lrho"] for i in step_infos)

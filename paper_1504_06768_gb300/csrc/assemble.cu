@@ -401,6 +401,7 @@ namespace {
 struct OpPrep {                       // H^T and, per collapse operator, C^T, C^+C, (C^+C)^T
     DeviceCSR Ht;
     std::vector<DeviceCSR> Ct, CtC, CtCt;
+    std::vector<OpSet> hops;          // host copy of the table (kept until the copy has run)
     OpSet* dops = nullptr;            // device table of the operator triples
 };
 
@@ -421,7 +422,8 @@ ss_status prep_ops(ss_ctx ctx, const DeviceCSR& H, const std::vector<DeviceCSR>&
     o.Ct.resize(n_c);
     o.CtC.resize(n_c);
     o.CtCt.resize(n_c);
-    std::vector<OpSet> hops(n_c);
+    std::vector<OpSet>& hops = o.hops;
+    hops.resize(n_c);
     for (int c = 0; c < n_c; ++c) {
         SS_TRY(transpose_csr(ctx, C[c], o.Ct[c]));
         SS_TRY(ctc_csr(ctx, C[c], o.Ct[c], o.CtC[c]));
@@ -433,7 +435,7 @@ ss_status prep_ops(ss_ctx ctx, const DeviceCSR& H, const std::vector<DeviceCSR>&
     SS_TRY(dev_alloc_n(ctx, &o.dops, (size_t)(n_c > 0 ? n_c : 1)));
     if (n_c > 0)
         SS_CUDA(ctx, cudaMemcpyAsync(o.dops, hops.data(), sizeof(OpSet) * n_c, cudaMemcpyHostToDevice, ctx->stream));
-    return SS_OK;       // (a copy from pageable memory has read hops when the call returns)
+    return SS_OK;
 }
 
 }  // namespace

@@ -25,12 +25,14 @@ double now_ms() {
 }
 
 struct PackedDev {                        // device arrays of one packed operand (per pattern)
-    int32_t *rows = nullptr, *col = nullptr, *src = nullptr, *ovb = nullptr, *ove = nullptr, *lvl = nullptr;
+    int32_t *col = nullptr, *src = nullptr, *lvl = nullptr;
+    int4* meta = nullptr;
     int32_t nunits = 0, G = 1, E = 1, nlev = 0;
 };
 
 struct PackedHost {
     std::vector<int32_t> rows, col, src, ovb, ove, lvl;
+    std::vector<int4> meta;               // {row, ovb, ove, 0} per unit row, as uploaded
     int32_t nunits = 0, G = 1, E = 1, nlev = 0;
 };
 
@@ -81,7 +83,7 @@ void pack_host(const std::vector<int32_t>& unit_rows, int G, const std::vector<i
         }
     std::sort(lens.begin(), lens.end());
     const int32_t p99 = lens.empty() ? 1 : lens[(size_t)(0.99 * (double)(lens.size() - 1))];
-    P.E = std::max(1, std::min(4, (p99 + G - 1) / G));
+    P.E = std::max(1, std::min(BATCH_MAXE, (p99 + G - 1) / G));
     P.rows = unit_rows;
     const size_t slots = (size_t)P.nunits * P.E * 32;
     P.col.assign(slots, -1);
@@ -194,11 +196,11 @@ ss_status upload_pattern(ss_ctx ctx, Pattern& P) {
         dv.nunits = h.nunits;
         dv.G = h.G;
         dv.E = h.E;
-        SS_TRY(upload_vec(ctx, h.rows, &dv.rows));
+        h.meta.resize(h.rows.size());
+        for (size_t k = 0; k < h.meta.size(); ++k) h.meta[k] = make_int4(h.rows[k], h.ovb[k], h.ove[k], 0);
+        SS_TRY(upload_vec(ctx, h.meta, &dv.meta));
         SS_TRY(upload_vec(ctx, h.col, &dv.col));
         SS_TRY(upload_vec(ctx, h.src, &dv.src));
-        SS_TRY(upload_vec(ctx, h.ovb, &dv.ovb));
-        SS_TRY(upload_vec(ctx, h.ove, &dv.ove));
         dv.nlev = h.nlev;
         if (h.nlev > 0) SS_TRY(upload_vec(ctx, h.lvl, &dv.lvl));
         return SS_OK;
@@ -220,11 +222,9 @@ ss_status upload_pattern(ss_ctx ctx, Pattern& P) {
 }
 
 void free_packed(ss_ctx ctx, PackedDev& d) {
-    dev_free(ctx, d.rows);
+    dev_free(ctx, d.meta);
     dev_free(ctx, d.col);
     dev_free(ctx, d.src);
-    dev_free(ctx, d.ovb);
-    dev_free(ctx, d.ove);
     dev_free(ctx, d.lvl);
 }
 
@@ -355,8 +355,6 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
         if (P->status != SS_OK) { ss_status e = set_error(ctx, P->status, P->error); cleanup(); return e; }
         BSTEP(upload_pattern(ctx, *P));
     }
-    int max_n = 0;
-    for (size_t q = 0; q < ns; ++q) max_n = std::max<int>(max_n, (int)blt.n[q]);
     // per-system buffers (one allocation) and descriptors; describe() lays
     // out system q's buffers from address base and returns the bytes used
     const size_t inner = mixed ? sizeof(float2) : sizeof(double2);
@@ -390,11 +388,10 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
         b.rho_out = rho_on_device ? reinterpret_cast<double2*>(rho_out[fastidx[q]])
                                   : reinterpret_cast<double2*>(take(n * sizeof(double2)));
         auto set_op = [&](PackedOp& o, const PackedDev& dv) {
-            o.rows = dv.rows;
+            o.meta = dv.meta;
             o.col = dv.col;
             o.src = dv.src;
-            o.ovb = dv.ovb;
-            o.ove = dv.ove;
+            o.dinv = nullptr;
             o.nunits = dv.nunits;
             o.G = dv.G;
             o.E = dv.E;
@@ -405,6 +402,7 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
         set_op(b.lo, P.lo);
         set_op(b.up, P.up);
         set_op(b.pa, P.pa);
+        b.up.dinv = reinterpret_cast<void*>(take((size_t)P.up.nunits * (((32 / P.up.G) * inner + 15) & ~size_t(15))));
         b.lvl_ptr = P.lvl_ptr;
         b.lvl_rows = P.lvl_rows;
         b.n_levels = P.n_levels;
@@ -441,7 +439,18 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
     bp.inner_rtol = opt.inner_rtol > 0 ? opt.inner_rtol : 1e-5;
     bp.power = 0;
     bp.seed = opt.seed;
-    BSTEP(batch_launch(ctx, dsys, (int)hs.size(), bp, max_n, ctl, ctl + 1));
+    // bulk copies stage the triangles' packed arrays: all must start on 16 bytes
+    bp.ring_allowed = 1;
+    auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    for (const BatchSys& b : hs)
+        for (const PackedOp* o : {&b.lo, &b.up})
+            if (!a16(o->meta) || !a16(o->col) || !a16(o->val) || (o->dinv && !a16(o->dinv))) bp.ring_allowed = 0;
+    std::vector<BatchShape> shapes(ns);
+    for (size_t q = 0; q < ns; ++q) {
+        const Pattern& P = *pats[pat_of[q]];
+        shapes[q] = BatchShape{(int32_t)blt.n[q], P.lo.nlev, P.up.nlev, P.lo.E, 32 / P.lo.G, P.up.E, 32 / P.up.G};
+    }
+    BSTEP(batch_launch(ctx, dsys, (int)hs.size(), bp, shapes, ctl, ctl + 1));
     SS_CUDA(ctx, cudaMemcpyAsync(hs.data(), dsys, sizeof(BatchSys) * hs.size(), cudaMemcpyDeviceToHost, ctx->stream));
     int herr = 0;
     SS_CUDA(ctx, cudaMemcpyAsync(&herr, ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

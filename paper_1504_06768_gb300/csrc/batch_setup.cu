@@ -309,7 +309,10 @@ ss_status batch_trace_systems(ss_ctx ctx, const std::vector<const ss_csr_view*>&
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(doff_d, doff.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, ctx->stream);
     if (ce != cudaSuccess) return fail(cuda_check(ctx, ce, "batch tables"));
+    // host staging of every slot stays alive until the stream is synchronised below
     std::vector<std::vector<StackEntry>> tabs(1 + nc_max);
+    std::vector<std::vector<int32_t>> rp_hs(1 + nc_max), col_hs(1 + nc_max);
+    std::vector<std::vector<double2>> val_hs(1 + nc_max);
     for (int slot = 0; slot <= nc_max; ++slot) {
         auto view = [&](int64_t s) -> const ss_csr_view* {
             if (slot == 0) return H[s];
@@ -330,8 +333,12 @@ ss_status batch_trace_systems(ss_ctx ctx, const std::vector<const ss_csr_view*>&
         if ((st = dev_alloc_n(ctx, &m.row_ptr, (size_t)D + 1)) != SS_OK) return fail(st);
         if ((st = dev_alloc_n(ctx, &m.col, (size_t)T)) != SS_OK) return fail(st);
         if ((st = dev_alloc_n(ctx, &m.val, (size_t)T)) != SS_OK) return fail(st);
-        std::vector<int32_t> rp_h(D + 1), col_h(any_host ? T : 0);
-        std::vector<double2> val_h(any_host ? T : 0);
+        std::vector<int32_t>& rp_h = rp_hs[slot];
+        std::vector<int32_t>& col_h = col_hs[slot];
+        std::vector<double2>& val_h = val_hs[slot];
+        rp_h.resize(D + 1);
+        col_h.resize(any_host ? T : 0);
+        val_h.resize(any_host ? T : 0);
         std::vector<StackEntry>& tab = tabs[slot];
         for (int64_t s = 0; s < ns; ++s) {
             const ss_csr_view* v = view(s);
@@ -376,7 +383,6 @@ ss_status batch_trace_systems(ss_ctx ctx, const std::vector<const ss_csr_view*>&
             dev_free(ctx, td);
             if (ce != cudaSuccess) return fail(cuda_check(ctx, ce, "operator stack"));
         }
-        // (host staging vectors are read by the pageable copies before they return)
     }
 
     // rows of every Liouvillian, with d spare slots on each row 0 for the trace row

@@ -102,7 +102,8 @@ __device__ __forceinline__ bool negligible(double2 a, double nu, double nv) {
 }
 
 // ------------------------------------------------------ triangular solves
-constexpr int MAXE = 3;    // packed entries per lane and unit
+constexpr int MAXE = BATCH_MAXE;    // packed entries per lane and unit
+constexpr int RING = BATCH_RING;    // shared-memory slots of the level ring (RING - 1 levels in flight)
 
 // One unit of a packed operand held in registers (a lane's slots, the row
 // and its CSR tail).
@@ -127,7 +128,10 @@ __device__ __forceinline__ void load_unit(const PackedOp& P, int32_t u, int lane
         r.vv[q] = zero<T>();
     }
     if (u >= P.nunits) return;
-    r.i = P.rows[u * R + grp];
+    const int4 m = P.meta[u * R + grp];
+    r.i = m.x;
+    r.ob = m.y;
+    r.oe = m.z;
 #pragma unroll
     for (int q = 0; q < MAXE; ++q)
         if (q < E) {
@@ -135,23 +139,16 @@ __device__ __forceinline__ void load_unit(const PackedOp& P, int32_t u, int lane
             r.jj[q] = P.col[slot];
             r.vv[q] = pv[slot];
         }
-    r.ob = P.ovb[u * R + grp];
-    r.oe = P.ove[u * R + grp];
 }
 
-// In-place triangular solve on the shared vector buf using the packed
-// operand P, one level at a time: the units of a level are spread over the
-// warps, a barrier separates levels, so every dependency of a row is complete
-// when its level starts and nothing waits on a flag.  LOWER: x_i = b_i -
-// sum_{j<i} l_ij x_j; UPPER: x_i = (b_i - sum_{j>i} u_ij x_j) / u_ii.
-// ocol/oval: the CSR of the factors for the entries of long rows that are not
-// packed.  Each warp loads its unit of the next level before the barrier.
+// Row update of a triangular solve on the shared vector buf: LOWER:
+// x_i = b_i - sum_{j<i} l_ij x_j; UPPER: x_i = (b_i - sum_{j>i} u_ij x_j) / u_ii
+// (dinv = 1 / u_ii).  The G lanes of a row split its entries and combine
+// them by shuffles; ocol/oval hold the CSR entries of long rows that are not
+// packed.
 template <bool LOWER, int G, class T>
-__device__ __forceinline__ void solve_unit(const UnitRegs<T>& cu, const int32_t* __restrict__ ocol,
-                                           const T* __restrict__ oval, const T* __restrict__ inv, T* buf,
-                                           int sub) {
-    T dinv = zero<T>();
-    if (!LOWER && cu.i >= 0 && sub == 0) dinv = inv[cu.i];
+__device__ __forceinline__ void solve_row(const UnitRegs<T>& cu, T dinv, const int32_t* __restrict__ ocol,
+                                          const T* __restrict__ oval, T* buf, int sub) {
     T acc = zero<T>();
 #pragma unroll
     for (int q = 0; q < MAXE; ++q)
@@ -170,22 +167,196 @@ __device__ __forceinline__ void solve_unit(const UnitRegs<T>& cu, const int32_t*
     }
 }
 
+// Shared-memory ring that stages the packed units of the next levels of a
+// triangular solve with bulk asynchronous copies (TMA), so that the data of a
+// level was requested RING - 1 levels earlier and the critical path of a
+// level is shared-memory latency, the arithmetic and one barrier.  One thread
+// issues a level's copies (values, columns, row records, inverse diagonal)
+// into a slot and arms the slot's mbarrier with their byte count; every
+// thread waits on the mbarrier's phase before reading the slot.  Levels are
+// numbered across calls (seq), slot = seq mod RING, phase parity =
+// (seq / RING) mod 2.
+struct Ring {
+    unsigned char* base;
+    uint64_t* bars;                 // RING mbarriers (shared)
+    int* abort;                     // shared flag: a wait ran out of time
+    int* err;                       // global error word
+    int32_t slot_bytes;
+    int32_t umax;                   // units per staged level (0: no ring)
+    uint32_t seq;                   // levels staged so far by this block
+};
+
+struct SlotLayout {
+    int32_t col, meta, dinv;        // byte offsets inside a slot (values at 0)
+};
+
+// Bytes of one unit's inverse diagonal (R values, padded to 16 bytes).
+template <class T>
+__host__ __device__ __forceinline__ int dinv_stride(int R) {
+    return (R * (int)sizeof(T) + 15) & ~15;
+}
+
+template <class T>
+__host__ __device__ __forceinline__ SlotLayout slot_layout(int E, int R, int umax) {
+    SlotLayout L;
+    L.col = umax * E * 32 * (int)sizeof(T);
+    L.meta = L.col + umax * E * 32 * 4;
+    L.dinv = L.meta + umax * R * 16;
+    return L;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t RING_WAIT_NS = 2000000000ull;   // 2 s: far beyond any copy; only a fault ends there
+
+// Wait for the phase of a slot; after RING_WAIT_NS the block gives up, raises
+// the error word and the abort flag, and later waits return at once.
+__device__ __forceinline__ void ring_wait(const Ring& rg, int slot, unsigned parity) {
+    if (mbar_try_wait(rg.bars + slot, parity)) return;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(rg.bars + slot, parity)) {
+        if (*(volatile int*)rg.abort) return;
+        if (globaltimer_ns() - t0 > RING_WAIT_NS) {
+            *(volatile int*)rg.abort = 1;
+            atomicExch(rg.err, 1);
+            return;
+        }
+    }
+}
+
+// One thread: copies of the first min(units, umax) units of level L into slot.
 template <bool LOWER, int G, class T>
-__device__ void cta_trsv_pk(const PackedOp& P, const int32_t* __restrict__ ocol, const T* __restrict__ oval,
-                            const T* __restrict__ inv, T* buf) {
+__device__ __forceinline__ void stage_level(const PackedOp& P, const int32_t* lvl, int32_t L, const Ring& rg,
+                                            int slot, const SlotLayout& sl) {
+    constexpr int R = 32 / G;
+    unsigned char* dst = rg.base + (size_t)slot * rg.slot_bytes;
+    uint64_t* bar = rg.bars + slot;
+    const int32_t beg = lvl[L];
+    const int32_t cnt = min(lvl[L + 1] - beg, rg.umax);
+    const int E = P.E;
+    const unsigned bv = (unsigned)(cnt * E * 32 * (int)sizeof(T));
+    const unsigned bc = (unsigned)(cnt * E * 32 * 4);
+    const unsigned bm = (unsigned)(cnt * R * 16);
+    const unsigned bd = LOWER ? 0u : (unsigned)(cnt * dinv_stride<T>(R));
+    mbar_arrive_tx(bar, bv + bc + bm + bd);
+    if (cnt > 0) {
+        bulk_g2s(dst, reinterpret_cast<const char*>(P.val) + (size_t)beg * E * 32 * sizeof(T), bv, bar);
+        bulk_g2s(dst + sl.col, P.col + (size_t)beg * E * 32, bc, bar);
+        bulk_g2s(dst + sl.meta, P.meta + (size_t)beg * R, bm, bar);
+        if (!LOWER)
+            bulk_g2s(dst + sl.dinv, reinterpret_cast<const char*>(P.dinv) + (size_t)beg * dinv_stride<T>(R), bd, bar);
+    }
+}
+
+// In-place level-scheduled triangular solve on the shared vector buf: the
+// units of a level are spread over the warps and a barrier separates levels,
+// so every dependency of a row is complete when its level starts and nothing
+// waits on a flag.  lvl: first unit of each level (nlev + 1 entries).
+template <bool LOWER, int G, class T>
+__device__ void cta_trsv_ring(const PackedOp& P, const int32_t* lvl, const int32_t* __restrict__ ocol,
+                              const T* __restrict__ oval, const T* __restrict__ inv, T* buf, Ring& rg) {
+    constexpr int R = 32 / G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane % G, grp = lane / G;
+    const int E = P.E, umax = rg.umax;
+    const int32_t nlev = P.nlev;
+    const SlotLayout sl = slot_layout<T>(E, R, umax);
+    const uint32_t s0 = rg.seq;
+    const int dstride = dinv_stride<T>(R) / (int)sizeof(T);
+    if (threadIdx.x == 0)
+        for (int32_t L = 0; L < RING - 1 && L < nlev; ++L) stage_level<LOWER, G, T>(P, lvl, L, rg, (s0 + L) % RING, sl);
+    for (int32_t l = 0; l < nlev; ++l) {
+        if (threadIdx.x == 0 && l + RING - 1 < nlev)
+            stage_level<LOWER, G, T>(P, lvl, l + RING - 1, rg, (s0 + l + RING - 1) % RING, sl);
+        const uint32_t q = s0 + l;
+        const int slot = q % RING;
+        ring_wait(rg, slot, (q / RING) & 1u);
+        const unsigned char* sb = rg.base + (size_t)slot * rg.slot_bytes;
+        const int32_t beg = lvl[l], cnt = lvl[l + 1] - beg;
+        for (int32_t u = warp; u < cnt; u += NW) {
+            UnitRegs<T> cu;
+            T dinv = zero<T>();
+            if (u < umax) {
+                const T* sv = reinterpret_cast<const T*>(sb);
+                const int32_t* sc = reinterpret_cast<const int32_t*>(sb + sl.col);
+                const int4 m = reinterpret_cast<const int4*>(sb + sl.meta)[u * R + grp];
+#pragma unroll
+                for (int q2 = 0; q2 < MAXE; ++q2) {
+                    cu.jj[q2] = q2 < E ? sc[(u * E + q2) * 32 + lane] : -1;
+                    cu.vv[q2] = q2 < E ? sv[(u * E + q2) * 32 + lane] : zero<T>();
+                }
+                cu.i = m.x;
+                cu.ob = m.y;
+                cu.oe = m.z;
+                if (!LOWER) dinv = reinterpret_cast<const T*>(sb + sl.dinv)[u * dstride + grp];
+            } else {
+                load_unit<G, T>(P, beg + u, lane, cu);
+                if (!LOWER && cu.i >= 0) dinv = inv[cu.i];
+            }
+            solve_row<LOWER, G, T>(cu, dinv, ocol, oval, buf, sub);
+        }
+        __syncthreads();
+    }
+    rg.seq = s0 + (uint32_t)nlev;
+}
+
+// Before a block leaves the kernel after an abandoned wait: wait (bounded)
+// for the copies still in flight into the ring.
+__device__ void ring_drain(const Ring& rg) {
+    if (threadIdx.x != 0 || rg.umax == 0 || !*(volatile int*)rg.abort) return;
+    for (int k = 1; k <= RING; ++k) {
+        if (rg.seq < (uint32_t)k) break;
+        const uint32_t q = rg.seq - k;
+        const uint64_t t0 = globaltimer_ns();
+        while (!mbar_try_wait(rg.bars + q % RING, (q / RING) & 1u))
+            if (globaltimer_ns() - t0 > RING_WAIT_NS) break;
+    }
+}
+
+// Without a ring: each warp loads its unit of the next level into registers
+// before the barrier of the current one.
+template <bool LOWER, int G, class T>
+__device__ void cta_trsv_pk(const PackedOp& P, const int32_t* lvl, const int32_t* __restrict__ ocol,
+                            const T* __restrict__ oval, const T* __restrict__ inv, T* buf) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane % G;
     UnitRegs<T> ua, ub;
-    int32_t beg = P.lvl[0], end = P.lvl[1];
+    int32_t beg = lvl[0], end = lvl[1];
     load_unit<G, T>(P, beg + warp < end ? beg + warp : P.nunits, lane, ua);
     for (int32_t l = 0; l < P.nlev; ++l) {
-        const int32_t nb = end, ne = (l + 1 < P.nlev) ? P.lvl[l + 2] : end;
-        // the first unit of the next level for this warp, in flight during this level
+        const int32_t nb = end, ne = (l + 1 < P.nlev) ? lvl[l + 2] : end;
         load_unit<G, T>(P, nb + warp < ne ? nb + warp : P.nunits, lane, ub);
-        solve_unit<LOWER, G, T>(ua, ocol, oval, inv, buf, sub);
+        solve_row<LOWER, G, T>(ua, (!LOWER && ua.i >= 0) ? inv[ua.i] : zero<T>(), ocol, oval, buf, sub);
         for (int32_t u = beg + warp + NW; u < end; u += NW) {      // wide levels: more units per warp
             UnitRegs<T> uc;
             load_unit<G, T>(P, u, lane, uc);
-            solve_unit<LOWER, G, T>(uc, ocol, oval, inv, buf, sub);
+            solve_row<LOWER, G, T>(uc, (!LOWER && uc.i >= 0) ? inv[uc.i] : zero<T>(), ocol, oval, buf, sub);
         }
         __syncthreads();
         ua = ub;
@@ -194,15 +365,23 @@ __device__ void cta_trsv_pk(const PackedOp& P, const int32_t* __restrict__ ocol,
     }
 }
 
+template <bool LOWER, int G, class T>
+__device__ __forceinline__ void cta_trsv_g(const PackedOp& P, const int32_t* lvl, const int32_t* ocol, const T* oval,
+                                           const T* inv, T* buf, Ring& rg) {
+    if (rg.umax > 0) cta_trsv_ring<LOWER, G, T>(P, lvl, ocol, oval, inv, buf, rg);
+    else cta_trsv_pk<LOWER, G, T>(P, lvl, ocol, oval, inv, buf);
+}
+
 template <bool LOWER, class T>
-__device__ void cta_trsv(const PackedOp& P, const int32_t* ocol, const T* oval, const T* inv, T* buf) {
+__device__ void cta_trsv(const PackedOp& P, const int32_t* lvl, const int32_t* ocol, const T* oval, const T* inv,
+                         T* buf, Ring& rg) {
     switch (P.G) {
-        case 1: cta_trsv_pk<LOWER, 1, T>(P, ocol, oval, inv, buf); break;
-        case 2: cta_trsv_pk<LOWER, 2, T>(P, ocol, oval, inv, buf); break;
-        case 4: cta_trsv_pk<LOWER, 4, T>(P, ocol, oval, inv, buf); break;
-        case 8: cta_trsv_pk<LOWER, 8, T>(P, ocol, oval, inv, buf); break;
-        case 16: cta_trsv_pk<LOWER, 16, T>(P, ocol, oval, inv, buf); break;
-        default: cta_trsv_pk<LOWER, 32, T>(P, ocol, oval, inv, buf); break;
+        case 1: cta_trsv_g<LOWER, 1, T>(P, lvl, ocol, oval, inv, buf, rg); break;
+        case 2: cta_trsv_g<LOWER, 2, T>(P, lvl, ocol, oval, inv, buf, rg); break;
+        case 4: cta_trsv_g<LOWER, 4, T>(P, lvl, ocol, oval, inv, buf, rg); break;
+        case 8: cta_trsv_g<LOWER, 8, T>(P, lvl, ocol, oval, inv, buf, rg); break;
+        case 16: cta_trsv_g<LOWER, 16, T>(P, lvl, ocol, oval, inv, buf, rg); break;
+        default: cta_trsv_g<LOWER, 32, T>(P, lvl, ocol, oval, inv, buf, rg); break;
     }
 }
 
@@ -275,6 +454,19 @@ __device__ void cta_pack_values(const PackedOp& P, const V* __restrict__ csr) {
     }
 }
 
+// Inverse diagonal of the upper factor in the packed row order of P (one
+// value per unit row; 0 for padding rows).
+template <class T>
+__device__ void cta_pack_dinv(const PackedOp& P, const T* __restrict__ inv) {
+    T* __restrict__ pd = reinterpret_cast<T*>(P.dinv);
+    const int R = 32 / P.G, ds = dinv_stride<T>(R) / (int)sizeof(T);
+    const int64_t total = (int64_t)P.nunits * R;
+    for (int64_t s = threadIdx.x; s < total; s += BT) {
+        const int32_t r = P.meta[s].x;
+        pd[(s / R) * ds + s % R] = r >= 0 ? inv[r] : zero<T>();
+    }
+}
+
 // -------------------------------------------------------------- context
 template <class T>
 struct Ctx {
@@ -284,10 +476,19 @@ struct Ctx {
     const T* fval;
     const T* finv;
     T* buf;                     // shared: n
-    volatile uint32_t* fl;      // shared: n
     double* red;                // shared reduction scratch
-    uint32_t epoch;
-    int* err;
+    const int32_t* lvl_lo;      // level boundaries of the two triangles (shared, or global)
+    const int32_t* lvl_up;
+    Ring* ring;
+};
+
+// Dynamic shared memory of one system: the solve vector, the level
+// boundaries of both triangles (when they fit) and the level ring.
+struct SmemPlan {
+    unsigned char* buf;
+    const int32_t* lvl_lo;
+    const int32_t* lvl_up;
+    Ring ring;
 };
 
 // out = M^{-1} in; the result also stays in the shared buffer
@@ -296,8 +497,8 @@ __device__ void cta_prec(Ctx<T>& c, const T* in, T* out) {
     const BatchSys& S = *c.S;
     for (int32_t i = threadIdx.x; i < c.n; i += BT) c.buf[i] = in[i];
     __syncthreads();
-    cta_trsv<true, T>(S.lo, S.f_col, c.fval, c.finv, c.buf);
-    cta_trsv<false, T>(S.up, S.f_col, c.fval, c.finv, c.buf);
+    cta_trsv<true, T>(S.lo, c.lvl_lo, S.f_col, c.fval, c.finv, c.buf, *c.ring);
+    cta_trsv<false, T>(S.up, c.lvl_up, S.f_col, c.fval, c.finv, c.buf, *c.ring);
     for (int32_t i = threadIdx.x; i < c.n; i += BT) out[i] = c.buf[i];
     // no barrier needed: the shared buffer is only read afterwards
 }
@@ -566,7 +767,7 @@ __device__ bool cta_ilu0(const BatchSys& S, bool mixed) {
 }
 
 // ------------------------------------------------------------- drivers
-__device__ void solve_fp64(BatchSys& S, const BatchParams& P, unsigned char* smem, double* red, int* err) {
+__device__ void solve_fp64(BatchSys& S, const BatchParams& P, SmemPlan& sm, double* red) {
     const int32_t n = S.n;
     Ctx<double2> c;
     c.S = &S;
@@ -574,12 +775,11 @@ __device__ void solve_fp64(BatchSys& S, const BatchParams& P, unsigned char* sme
     c.aval = S.a_val;
     c.fval = S.f_val;
     c.finv = S.f_inv;
-    c.buf = reinterpret_cast<double2*>(smem);
-    c.fl = reinterpret_cast<volatile uint32_t*>(smem + sizeof(double2) * n);
+    c.buf = reinterpret_cast<double2*>(sm.buf);
     c.red = red;
-    c.epoch = 1;
-    c.err = err;
-    for (int32_t i = threadIdx.x; i < n; i += BT) c.fl[i] = 0u;
+    c.lvl_lo = sm.lvl_lo;
+    c.lvl_up = sm.lvl_up;
+    c.ring = &sm.ring;
     double2* wk = reinterpret_cast<double2*>(S.work);
     double2* b = wk + 8 * (size_t)n;
     double2* x = S.x64;
@@ -649,7 +849,7 @@ __device__ double true_residual(const BatchSys& S, const double2* __restrict__ x
 constexpr double DELTA = 0.05;
 constexpr int REFRESH = 50;
 
-__device__ void solve_mixed(BatchSys& S, const BatchParams& P, unsigned char* smem, double* red, int* err) {
+__device__ void solve_mixed(BatchSys& S, const BatchParams& P, SmemPlan& sm, double* red) {
     using T = float2;
     using A = float;
     const int32_t n = S.n;
@@ -659,11 +859,11 @@ __device__ void solve_mixed(BatchSys& S, const BatchParams& P, unsigned char* sm
     c.aval = S.a_val32;
     c.fval = S.f_val32;
     c.finv = S.f_inv32;
-    c.buf = reinterpret_cast<float2*>(smem);
-    c.fl = reinterpret_cast<volatile uint32_t*>(smem + sizeof(float2) * n);
+    c.buf = reinterpret_cast<float2*>(sm.buf);
     c.red = red;
-    c.epoch = 1;
-    c.err = err;
+    c.lvl_lo = sm.lvl_lo;
+    c.lvl_up = sm.lvl_up;
+    c.ring = &sm.ring;
     T* r = reinterpret_cast<float2*>(S.work);
     T* rhat = r + n;
     T* p = rhat + n;
@@ -818,6 +1018,16 @@ __global__ void __launch_bounds__(BT, 1) batched_solver(BatchSys* sys, int nsys,
     // The system's descriptor is copied to shared memory: kept in global
     // memory, its pointer fields would be re-read from L2 after every store.
     __shared__ __align__(16) BatchSys S;
+    __shared__ __align__(8) uint64_t ring_bars[RING];
+    __shared__ int ring_abort;
+    if (threadIdx.x == 0) {
+        for (int r = 0; r < RING; ++r) mbar_init(ring_bars + r, 1);
+        ring_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t ring_seq = 0;          // levels staged by this block (identical in every thread)
+    Ring last{};
     while (true) {
         if (threadIdx.x == 0) s_idx = atomicAdd(queue, 1);
         __syncthreads();
@@ -846,14 +1056,46 @@ __global__ void __launch_bounds__(BT, 1) batched_solver(BatchSys* sys, int nsys,
             cta_pack_values<float2>(S.lo, S.f_val32);
             cta_pack_values<float2>(S.up, S.f_val32);
             cta_pack_values<float2>(S.pa, S.a_val32);
+            cta_pack_dinv<float2>(S.up, S.f_inv32);
         } else {
             cta_pack_values<double2>(S.lo, S.f_val);
             cta_pack_values<double2>(S.up, S.f_val);
             cta_pack_values<double2>(S.pa, S.a_val);
+            cta_pack_dinv<double2>(S.up, S.f_inv);
+        }
+        // the packed operands are read by bulk copies (the async proxy) from here on
+        asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        // shared memory of this system: vector, level boundaries, ring
+        SmemPlan sm;
+        {
+            const size_t vb = ((size_t)S.n * (MIXED ? sizeof(float2) : sizeof(double2)) + 15) & ~size_t(15);
+            sm.buf = smem;
+            int32_t* lv = reinterpret_cast<int32_t*>(smem + vb);
+            size_t off = vb;
+            if (P.lvl_smem) {
+                const int nlo = S.lo.nlev + 1, nup = S.up.nlev + 1;
+                for (int t = threadIdx.x; t < nlo; t += BT) lv[t] = S.lo.lvl[t];
+                for (int t = threadIdx.x; t < nup; t += BT) lv[nlo + t] = S.up.lvl[t];
+                sm.lvl_lo = lv;
+                sm.lvl_up = lv + nlo;
+                off += ((size_t)(nlo + nup) * 4 + 15) & ~size_t(15);
+            } else {
+                sm.lvl_lo = S.lo.lvl;
+                sm.lvl_up = S.up.lvl;
+            }
+            sm.ring.base = smem + off;
+            sm.ring.bars = ring_bars;
+            sm.ring.abort = &ring_abort;
+            sm.ring.err = err;
+            sm.ring.slot_bytes = P.ring_slot_bytes;
+            sm.ring.umax = P.ring_umax;
+            sm.ring.seq = ring_seq;
         }
         __syncthreads();
-        if (MIXED) solve_mixed(S, P, smem, red, err);
-        else solve_fp64(S, P, smem, red, err);
+        if (MIXED) solve_mixed(S, P, sm, red);
+        else solve_fp64(S, P, sm, red);
+        ring_seq = sm.ring.seq;
+        last = sm.ring;
         finalise(S, red);
         if (threadIdx.x == 0) {
             sys[k].status = S.status;
@@ -863,21 +1105,71 @@ __global__ void __launch_bounds__(BT, 1) batched_solver(BatchSys* sys, int nsys,
         }
         __syncthreads();
     }
+    ring_drain(last);
 }
 
 }  // namespace
-
-size_t batch_smem_bytes(int n, bool mixed) {
-    return (size_t)n * ((mixed ? sizeof(float2) : sizeof(double2)) + sizeof(uint32_t));
-}
 
 int batch_max_n(bool mixed) {
     const size_t cap = 227 * 1024 - 2048;
     return (int)(cap / ((mixed ? sizeof(float2) : sizeof(double2)) + sizeof(uint32_t)));
 }
 
-ss_status batch_launch(ss_ctx ctx, BatchSys* dsys, int nsys, const BatchParams& p, int max_n, int* queue, int* err) {
-    const size_t smem = batch_smem_bytes(max_n, p.mixed != 0);
+namespace {
+
+template <class T>
+size_t slot_bytes_of(int E, int R, int umax) {
+    const SlotLayout L = slot_layout<T>(E, R, umax);
+    return (size_t)L.dinv + (size_t)umax * dinv_stride<T>(R);
+}
+
+// Dynamic shared memory of a launch for a given plan (lvl_smem, umax).
+template <class T>
+size_t plan_bytes(const std::vector<BatchShape>& shapes, int lvl_smem, int umax, size_t* slot_out) {
+    size_t base = 0, slot = 0;
+    for (const BatchShape& b : shapes) {
+        size_t v = ((size_t)b.n * sizeof(T) + 15) & ~size_t(15);
+        if (lvl_smem) v += ((size_t)(b.nlev_lo + b.nlev_up + 2) * 4 + 15) & ~size_t(15);
+        base = std::max(base, v);
+        if (umax > 0)
+            slot = std::max(slot, std::max(slot_bytes_of<T>(b.E_lo, b.R_lo, umax), slot_bytes_of<T>(b.E_up, b.R_up, umax)));
+    }
+    *slot_out = slot;
+    return base + (size_t)RING * slot;
+}
+
+template <class T>
+size_t choose_plan(const std::vector<BatchShape>& shapes, size_t cap, BatchParams& p) {
+    for (int lvl_smem = 1; lvl_smem >= 0; --lvl_smem)
+        for (int umax = p.ring_allowed ? NW : 0; umax >= 1; umax >>= 1) {
+            size_t slot = 0;
+            const size_t b = plan_bytes<T>(shapes, lvl_smem, umax, &slot);
+            if (b <= cap) {
+                p.lvl_smem = lvl_smem;
+                p.ring_umax = umax;
+                p.ring_slot_bytes = (int)slot;
+                return b;
+            }
+        }
+    size_t slot = 0;
+    p.lvl_smem = 0;
+    p.ring_umax = 0;
+    p.ring_slot_bytes = 0;
+    return plan_bytes<T>(shapes, 0, 0, &slot);
+}
+
+}  // namespace
+
+ss_status batch_launch(ss_ctx ctx, BatchSys* dsys, int nsys, BatchParams p, const std::vector<BatchShape>& shapes,
+                       int* queue, int* err) {
+    int optin = 0;
+    SS_CUDA(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    cudaFuncAttributes fa;
+    if (p.mixed) SS_CUDA(ctx, cudaFuncGetAttributes(&fa, batched_solver<true>));
+    else SS_CUDA(ctx, cudaFuncGetAttributes(&fa, batched_solver<false>));
+    const size_t cap = (size_t)optin > fa.sharedSizeBytes + 256 ? (size_t)optin - fa.sharedSizeBytes - 256 : 0;
+    const size_t smem = p.mixed ? choose_plan<float2>(shapes, cap, p) : choose_plan<double2>(shapes, cap, p);
+    if (smem > cap) return set_error(ctx, SS_ERR_UNSUPPORTED, "system too large for the per-system solver's shared memory");
     const int grid = std::max(1, std::min(nsys, ctx->num_sms > 0 ? ctx->num_sms : 1));
     if (p.mixed) {
         SS_CUDA(ctx, cudaFuncSetAttribute(batched_solver<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -10,6 +10,8 @@
 #include "common.cuh"
 
 constexpr int BATCH_THREADS = 512;
+constexpr int BATCH_MAXE = 3;       // packed entry slots per lane and unit (longer rows overflow to the CSR)
+constexpr int BATCH_RING = 4;       // shared-memory slots staging triangular-solve levels
 
 // Lane-major packed layout of one CSR operand (a strict triangle of the
 // factors, or A itself).  Rows are grouped into units of R = 32 / G rows
@@ -18,12 +20,12 @@ constexpr int BATCH_THREADS = 512;
 // with E coalesced loads.  Entries of a long row beyond its first E*G stay in
 // the CSR and are visited from ovb to ove.
 struct PackedOp {
-    const int32_t* rows;    // nunits * R row ids (-1 pads a unit)
+    const int4* meta;       // nunits * R row records {row (-1 pads a unit), first CSR position
+                            // not packed, end of the row's CSR range, 0}
     const int32_t* col;     // nunits * E * 32 column ids (-1: empty slot)
     const int32_t* src;     // nunits * E * 32 CSR positions of the slots (-1: empty)
-    const int32_t* ovb;     // nunits * R: first CSR position not packed
-    const int32_t* ove;     // nunits * R: end of the row's CSR range
     void* val;              // per system: nunits * E * 32 values of the inner type
+    void* dinv;             // per system, upper triangle: nunits * R values 1 / u_ii (else null)
     int32_t nunits, G, E;
     const int32_t* lvl;     // triangles: first unit of each level (nlev + 1 entries)
     int32_t nlev;
@@ -73,6 +75,15 @@ struct BatchParams {
     double inner_rtol;          // mixed: inner relative tolerance
     int power;                  // inverse power (FP64 only)
     uint64_t seed;
+    int ring_allowed;           // every staged array is 16-byte aligned (bulk copies may be used)
+    // shared-memory plan of the launch (set by batch_launch)
+    int ring_umax;              // units per staged level (0: no ring)
+    int ring_slot_bytes;
+    int lvl_smem;               // level boundaries copied to shared memory
+};
+
+struct BatchShape {             // what the shared-memory plan needs of one system
+    int32_t n, nlev_lo, nlev_up, E_lo, R_lo, E_up, R_up;
 };
 
 // ------------------------------------------------------- batched setup
@@ -119,6 +130,8 @@ ss_status batch_download_pattern(ss_ctx ctx, const BatchLt& b, int s, std::vecto
                                  std::vector<int32_t>& col);
 ss_status batch_gather_values(ss_ctx ctx, const BatchLt& b, const std::vector<GatherEntry>& tab);
 
-size_t batch_smem_bytes(int n, bool mixed);
 int batch_max_n(bool mixed);
-ss_status batch_launch(ss_ctx ctx, BatchSys* dsys, int nsys, const BatchParams& p, int max_n, int* queue, int* err);
+// Chooses the shared-memory plan (ring size, level boundaries in shared
+// memory) for the systems' shapes and launches the persistent solver.
+ss_status batch_launch(ss_ctx ctx, BatchSys* dsys, int nsys, BatchParams p, const std::vector<BatchShape>& shapes,
+                       int* queue, int* err);
