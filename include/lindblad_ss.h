@@ -275,6 +275,52 @@ ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_view* H, cons
                                const ss_csr_view* const* c_ops, const ss_options* opt,
                                double* const* rho_out, int rho_on_device, ss_info* infos);
 
+/* -------------------------------------------------------------- serving */
+
+/* A serving loop for steady-state requests (not part of the paper's method:
+ * an interface around it).  Requests of different Hilbert sizes are
+ * submitted at any time and solved while others are on the device: a worker
+ * thread admits queued requests in arrival order whenever a batch slot is
+ * free and the request's estimated device footprint fits the memory budget,
+ * and runs them as one batch ("wave") of the persistent per-system solver of
+ * steady_state_batched on the slot's own stream; several waves run side by
+ * side, each system holding one SM, so a new wave fills the SMs an earlier
+ * one leaves idle.  Pattern analyses (RCM ordering, level schedule) stay
+ * resident across waves for requests with the same structure.  Requests
+ * outside the persistent solver's scope (n beyond its limit, or options it
+ * does not run) go to a second lane running steady_state().  A request's
+ * result is the one the same system gets alone from steady_state_batched
+ * (or from steady_state in the second lane). */
+typedef struct ss_server_s* ss_server;
+
+typedef struct {
+    double hbm_budget_mb;   /* device memory admitted requests may hold (MiB); <= 0: 80 % of the free memory */
+    int max_waves;          /* batches in flight at once (default 4) */
+    int max_wave_systems;   /* systems per batch; <= 0: number of SMs / max_waves */
+} ss_server_options;
+
+void ss_server_options_default(ss_server_options* so);
+/* opt: the solve options of every request (NULL: defaults).  Starts the worker threads. */
+ss_status ss_server_create(int device, const ss_options* opt, const ss_server_options* so, ss_server* out);
+/* Finishes every submitted request, stops the workers and frees the server. */
+ss_status ss_server_destroy(ss_server s);
+/* Queues one system (host CSR views, copied before the call returns).
+ * rho_out: host memory for d*d complex values (column-major), written when the
+ * request completes; it must stay valid until then.  *ticket identifies the
+ * request.  SS_ERR_OOM when its footprint exceeds the whole budget. */
+ss_status ss_submit(ss_server s, const ss_csr_view* H, int n_c, const ss_csr_view* c_ops, double* rho_out,
+                    uint64_t* ticket);
+/* *done = 1 once the request has completed. */
+ss_status ss_poll(ss_server s, uint64_t ticket, int* done);
+/* Waits up to timeout_us (< 0: without limit).  Returns SS_ERR_TIMEOUT while the
+ * request is pending (it stays queryable); once it has completed, returns its
+ * solve status, fills info (may be NULL) and *latency_ms (submission to
+ * completion, may be NULL) and forgets the ticket. */
+ss_status ss_wait(ss_server s, uint64_t ticket, int64_t timeout_us, ss_info* info, double* latency_ms);
+/* Waves launched, requests completed, memory held by admitted requests and the budget. */
+ss_status ss_server_stats(ss_server s, uint64_t* waves, uint64_t* completed, double* in_use_mb, double* budget_mb);
+const char* ss_server_last_error(ss_server s);
+
 /* ---------------------------------------------------------- diagnostics */
 
 /* Kernel classes of the per-launch profiler. */

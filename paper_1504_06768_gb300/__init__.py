@@ -23,7 +23,8 @@ from . import _binding as B
 __all__ = ["SolverError", "Context", "Matrix", "Preconditioner", "get_context", "assemble_liouvillian",
            "add_trace_row", "add_shift", "rcm_permute", "permute", "bandwidth_profile", "ilu_factor",
            "spmv", "spmv_f32", "precond_apply", "precond_apply_f32", "krylov_solve", "steady_state",
-           "steady_state_batched", "krylov_solve_noalloc", "NOALLOC_MAX_N", "library_path"]
+           "steady_state_batched", "krylov_solve_noalloc", "NOALLOC_MAX_N", "library_path",
+           "assemble_trace_batched", "Server"]
 
 NOALLOC_MAX_N = 65536
 
@@ -401,3 +402,87 @@ def steady_state(H, c_ops: Sequence, method: str = "iterative-bicgstab", tol: fl
         ctx.check(st, "steady_state")
     result = rho.reshape((d, d), order="F") if out is None else out.view(d, d).T
     return result, info.as_dict()
+
+
+class Server:
+    """Serving loop (ss_server_*): submit steady-state requests at any time,
+    wait for them by ticket.  Inputs are copied at submission; each result is
+    written to a host buffer that this object keeps until the request is
+    waited for."""
+
+    def __init__(self, method: str = "iterative-bicgstab", tol: float = 1e-10, precond: str = "ilu0",
+                 precision: str = "mixed", maxiter: int = 1000, restart: int = 30, drop_tol: float = 1e-4,
+                 fill_factor: float = 10.0, w: float = 0.0, sigma: float = 1e-15, use_rcm: bool = True,
+                 seed: int = 0, inner_rtol: float = 1e-5, hbm_budget_mb: float = 0.0, max_waves: int = 4,
+                 max_wave_systems: int = 0, device: int = 0):
+        lib = B.load()
+        opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm,
+                       seed, inner_rtol)
+        so = B.ServerOptions()
+        lib.ss_server_options_default(C.byref(so))
+        so.hbm_budget_mb = hbm_budget_mb
+        so.max_waves = max_waves
+        so.max_wave_systems = max_wave_systems
+        h = C.c_void_p()
+        st = lib.ss_server_create(device, C.byref(opt), C.byref(so), C.byref(h))
+        if st != 0:
+            raise SolverError(st, "ss_server_create failed")
+        self.handle = h
+        self._out = {}
+
+    def _check(self, st, what):
+        if st != 0:
+            raise SolverError(st, f"{what}: {B.load().ss_server_last_error(self.handle).decode()}")
+
+    def submit(self, H, c_ops) -> int:
+        hv = _CsrHost(H)
+        cvs = [_CsrHost(c) for c in c_ops]
+        arr = (B.CsrView * max(len(cvs), 1))(*[c.view for c in cvs])
+        d = hv.view.n_rows
+        rho = np.empty(d * d, dtype=np.complex128)
+        t = C.c_uint64()
+        self._check(B.load().ss_submit(self.handle, C.byref(hv.view), len(cvs), arr, rho.ctypes.data, C.byref(t)),
+                    "ss_submit")
+        self._out[t.value] = (rho, d)
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        done = C.c_int()
+        self._check(B.load().ss_poll(self.handle, ticket, C.byref(done)), "ss_poll")
+        return bool(done.value)
+
+    def wait(self, ticket: int, timeout_s: Optional[float] = None, raise_on_failure: bool = True):
+        """Returns (rho (d x d), info dict, latency in ms)."""
+        info = B.Info()
+        lat = C.c_double()
+        us = -1 if timeout_s is None else int(timeout_s * 1e6)
+        st = B.load().ss_wait(self.handle, ticket, us, C.byref(info), C.byref(lat))
+        if st == B.SS_ERR_TIMEOUT and not self.poll(ticket):
+            raise TimeoutError(f"request {ticket} still pending")
+        rho, d = self._out.pop(ticket)
+        if st != 0 and (raise_on_failure or st not in (B.SS_NOT_CONVERGED, B.SS_BREAKDOWN)):
+            self._check(st, "ss_wait")
+        return rho.reshape((d, d), order="F"), info.as_dict(), lat.value
+
+    def stats(self):
+        waves, done = C.c_uint64(), C.c_uint64()
+        used, budget = C.c_double(), C.c_double()
+        self._check(B.load().ss_server_stats(self.handle, C.byref(waves), C.byref(done), C.byref(used),
+                                             C.byref(budget)), "ss_server_stats")
+        return {"waves": waves.value, "completed": done.value, "in_use_mb": used.value, "budget_mb": budget.value}
+
+    def close(self):
+        if self.handle is not None:
+            B.load().ss_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and B._lib is not None:
+            B._lib.ss_server_destroy(self.handle)
+            self.handle = None

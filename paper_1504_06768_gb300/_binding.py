@@ -55,6 +55,10 @@ _I64P = C.POINTER(C.c_int64)
 _I32P = C.POINTER(C.c_int32)
 _DP = C.POINTER(C.c_double)
 
+class ServerOptions(C.Structure):
+    _fields_ = [("hbm_budget_mb", C.c_double), ("max_waves", C.c_int), ("max_wave_systems", C.c_int)]
+
+
 _SIGNATURES = {
     "ss_ctx_create": (C.c_int, [C.c_int, _P, _PP]),
     "ss_ctx_destroy": (C.c_int, [_P]),
@@ -92,6 +96,14 @@ _SIGNATURES = {
     "krylov_solve_noalloc": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int, C.POINTER(C.c_int), _DP]),
     "steady_state": (C.c_int, [_P, C.POINTER(CsrView), C.c_int, C.POINTER(CsrView), C.POINTER(Options),
                                _P, C.c_int, C.POINTER(Info)]),
+    "ss_server_options_default": (None, [C.POINTER(ServerOptions)]),
+    "ss_server_create": (C.c_int, [C.c_int, C.POINTER(Options), C.POINTER(ServerOptions), _PP]),
+    "ss_server_destroy": (C.c_int, [_P]),
+    "ss_submit": (C.c_int, [_P, C.POINTER(CsrView), C.c_int, C.POINTER(CsrView), _P, C.POINTER(C.c_uint64)]),
+    "ss_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_int)]),
+    "ss_wait": (C.c_int, [_P, C.c_uint64, C.c_int64, C.POINTER(Info), _DP]),
+    "ss_server_stats": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), _DP, _DP]),
+    "ss_server_last_error": (C.c_char_p, [_P]),
 }
 
 _lib = None

@@ -1,21 +1,22 @@
 // steady_state_batched: many independent systems solved by one persistent
-// launch of the per-system CTA solver.  Systems that share a sparsity pattern
-// (parameter sweeps) share the RCM ordering, the level schedule and the
-// triangular-solve units, which are computed once per pattern on the host.
+// launch of the per-system CTA solver, organised as a wave (batch_wave.cuh).
+// Systems that share a sparsity pattern (parameter sweeps) share the RCM
+// ordering, the level schedule and the triangular-solve units, computed once
+// per pattern on the host (and, in the serving loop, once per pattern across
+// waves through the PatternCache).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 #include <map>
-#include <string>
-#include <tuple>
 #include <memory>
 #include <new>
+#include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
-#include "batched.cuh"
-#include "common.cuh"
+#include "batch_wave.cuh"
 
 namespace {
 
@@ -23,36 +24,6 @@ double now_ms() {
     using namespace std::chrono;
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
-
-struct PackedDev {                        // device arrays of one packed operand (per pattern)
-    int32_t *col = nullptr, *src = nullptr, *lvl = nullptr;
-    int4* meta = nullptr;
-    int32_t nunits = 0, G = 1, E = 1, nlev = 0;
-};
-
-struct PackedHost {
-    std::vector<int32_t> rows, col, src, ovb, ove, lvl;
-    std::vector<int4> meta;               // {row, ovb, ove, 0} per unit row, as uploaded
-    int32_t nunits = 0, G = 1, E = 1, nlev = 0;
-};
-
-struct Pattern {                          // per distinct pattern of L~ (before ordering)
-    std::vector<int32_t> rp, col;         // natural-order pattern
-    int64_t d = 0;
-    std::vector<int32_t> perm, iperm, tidx;
-    int32_t r0 = 0;
-    // host products of the analysis (uploaded by upload_pattern)
-    std::vector<int32_t> prp, pcol, map, dpos, lorder, lptr, lunits, uunits;
-    PackedHost hl, hu, ha;
-    ss_status status = SS_OK;
-    std::string error;
-    // device arrays of the permuted structure
-    int32_t *prp_d = nullptr, *pcol_d = nullptr, *map_d = nullptr;
-    int32_t *perm_d = nullptr, *tidx_d = nullptr, *dpos_d = nullptr;
-    int32_t *lo_units = nullptr, *up_units = nullptr, *lvl_ptr = nullptr, *lvl_rows = nullptr;
-    int32_t lo_nunits = 0, up_nunits = 0, lo_g = 1, up_g = 1, a_g = 1, n_levels = 0, up_levels = 0;
-    PackedDev lo, up, pa;
-};
 
 int lanes_for(double avg) {
     int g = 1;
@@ -218,148 +189,184 @@ ss_status upload_pattern(ss_ctx ctx, Pattern& P) {
     SS_TRY(upload_vec(ctx, P.uunits, &P.up_units));
     SS_TRY(upload_vec(ctx, P.lptr, &P.lvl_ptr));
     SS_TRY(upload_vec(ctx, P.lorder, &P.lvl_rows));
+    SS_TRY(upload_vec(ctx, P.rp, &P.rp_d));
+    SS_TRY(upload_vec(ctx, P.col, &P.col_d));
     return SS_OK;
-}
-
-void free_packed(ss_ctx ctx, PackedDev& d) {
-    dev_free(ctx, d.meta);
-    dev_free(ctx, d.col);
-    dev_free(ctx, d.src);
-    dev_free(ctx, d.lvl);
-}
-
-void free_pattern(ss_ctx ctx, Pattern& P) {
-    free_packed(ctx, P.lo);
-    free_packed(ctx, P.up);
-    free_packed(ctx, P.pa);
-    dev_free(ctx, P.prp_d);
-    dev_free(ctx, P.pcol_d);
-    dev_free(ctx, P.map_d);
-    dev_free(ctx, P.perm_d);
-    dev_free(ctx, P.tidx_d);
-    dev_free(ctx, P.dpos_d);
-    dev_free(ctx, P.lo_units);
-    dev_free(ctx, P.up_units);
-    dev_free(ctx, P.lvl_ptr);
-    dev_free(ctx, P.lvl_rows);
 }
 
 }  // namespace
 
-extern "C" ss_status steady_state(ss_ctx, const ss_csr_view*, int, const ss_csr_view*, const ss_options*, double*, int,
-                                  ss_info*);
+Pattern::~Pattern() {
+    cudaSetDevice(device);
+    void* ptrs[] = {rp_d, col_d, prp_d, pcol_d, map_d, perm_d, tidx_d, dpos_d, lo_units, up_units, lvl_ptr, lvl_rows,
+                    lo.col, lo.src, lo.lvl, lo.meta, up.col, up.src, up.lvl, up.meta, pa.col, pa.src, pa.lvl, pa.meta};
+    for (void* q : ptrs)
+        if (q) cudaFreeAsync(q, 0);
+}
 
-extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_view* H, const int* n_c,
-                                          const ss_csr_view* const* c_ops, const ss_options* opt_in,
-                                          double* const* rho_out, int rho_on_device, ss_info* infos) {
-    if (!ctx) return SS_ERR_INVALID;
-    SS_CUDA(ctx, cudaSetDevice(ctx->device));
-    if (n_sys < 0 || (n_sys > 0 && (!H || !n_c || !rho_out))) return set_error(ctx, SS_ERR_INVALID, "null argument");
-    ss_options opt;
-    ss_options_default(&opt);
-    if (opt_in) opt = *opt_in;
+void PatternCache::touch(const PatternKey& k, const std::shared_ptr<Pattern>& p) {
+    for (size_t i = 0; i < lru.size(); ++i)
+        if (lru[i].second == p) {
+            auto e = lru[i];
+            lru.erase(lru.begin() + (long)i);
+            lru.push_back(e);
+            return;
+        }
+    lru.emplace_back(k, p);
+}
+
+void PatternCache::insert(const PatternKey& k, const std::shared_ptr<Pattern>& p) {
+    by_key[k].push_back(p);
+    touch(k, p);
+    while (lru.size() > max_patterns) {          // evict the least recently used (waves keep their own references)
+        auto e = lru.front();
+        lru.erase(lru.begin());
+        auto& v = by_key[e.first];
+        v.erase(std::remove(v.begin(), v.end(), e.second), v.end());
+        if (v.empty()) by_key.erase(e.first);
+    }
+}
+
+size_t wave_footprint_bytes(int64_t d, int64_t nnz_h, const std::vector<int64_t>& nnz_c,
+                            const std::vector<int64_t>& ctc_c, bool mixed) {
+    // nnz(L) <= 2 d nnz(H) + sum_k (nnz(C_k)^2 + 2 d nnz(C_k^+ C_k)) + d (trace row), the
+    // candidate count of the assembly; ctc_c bounds nnz(C_k^+ C_k)
+    double nnz = 2.0 * (double)d * (double)nnz_h + (double)d;
+    for (size_t k = 0; k < nnz_c.size(); ++k)
+        nnz += (double)nnz_c[k] * (double)nnz_c[k] + 2.0 * (double)d * (double)ctc_c[k];
+    const double n = (double)d * (double)d;
+    // per stored entry: A and the factors (FP64), their FP32 copies, three
+    // packed operands with lane padding, and the assembly's candidates
+    // (transient); per row: the Krylov vectors and the per-row arrays
+    const double per_nnz = 16.0 + 16.0 + (mixed ? 16.0 : 0.0) + 4.0 * (mixed ? 8.0 : 16.0) + 24.0;
+    const double per_row = 10.0 * (mixed ? 8.0 : 16.0) + 5.0 * 16.0;
+    return (size_t)(std::min(nnz, n * n) * per_nnz + n * per_row) + (1u << 16);
+}
+
+size_t wave_pinned_bytes(const BatchWave& w) {
+    size_t b = ((w.H.size() * sizeof(BatchSys) + 255) & ~size_t(255)) + 256;
+    if (!w.rho_on_device)
+        for (const ss_csr_view* h : w.H) b += (size_t)h->n_rows * h->n_rows * sizeof(double2);
+    return b;
+}
+
+bool wave_ready(BatchWave& w) {
+    if (!w.launched) return true;
+    return cudaEventQuery(w.done) != cudaErrorNotReady;
+}
+
+void wave_release(BatchWave& w) {
+    ss_ctx ctx = w.ctx;
+    batch_lt_free(ctx, w.blt);
+    for (void* p : w.owned) dev_free(ctx, p);
+    w.owned.clear();
+    w.pats.clear();
+    w.pat_of.clear();
+    if (w.done) {
+        cudaEventDestroy(w.done);
+        w.done = nullptr;
+    }
+    w.launched = false;
+}
+
+ss_status wave_begin(BatchWave& w) {
+    ss_ctx ctx = w.ctx;
+    const ss_options& opt = w.opt;
     const bool mixed = opt.precision == SS_PREC_MIXED;
-    const bool fast = opt.method == SS_METHOD_ITER_BICGSTAB && opt.precond == SS_PRECOND_ILU0;
-    const int max_n_fast = batch_max_n(mixed);
-    const double t0 = now_ms();
-    std::vector<int> slow;
-    std::vector<int> fastidx;
-    for (int k = 0; k < n_sys; ++k) {
-        const int64_t d = H[k].n_rows;
-        if (fast && d > 0 && d * d <= max_n_fast) fastidx.push_back(k);
-        else slow.push_back(k);
-    }
-    // systems outside the persistent kernel's scope: the single-system path
-    ss_status worst = SS_OK;
-    for (int k : slow) {
-        ss_info inf{};
-        ss_status st = steady_state(ctx, &H[k], n_c[k], n_c[k] ? c_ops[k] : nullptr, &opt, rho_out[k],
-                                    rho_on_device, &inf);
-        if (infos) infos[k] = inf;
-        if (st != SS_OK && st != SS_NOT_CONVERGED && st != SS_BREAKDOWN) return st;
-        if (st != SS_OK) worst = st;
-    }
-    if (fastidx.empty()) return worst;
-
-    // ------------------------------------------------------------ setup
-    // (1) every system's L~ with a fixed number of launches; (2) systems that
-    // share a pattern (hash, then an exact check on the device) share one RCM
-    // ordering, level schedule and packing, analysed on host threads, one per
-    // distinct pattern; (3) one gather puts every system's values in its
-    // pattern's order.
-    const size_t ns = fastidx.size();
-    std::vector<const ss_csr_view*> Hv(ns), Cv(ns);
-    std::vector<int> ncv(ns);
-    for (size_t q = 0; q < ns; ++q) {
-        const int k = fastidx[q];
-        Hv[q] = &H[k];
-        ncv[q] = n_c[k];
-        Cv[q] = n_c[k] ? c_ops[k] : nullptr;
-    }
-    BatchLt blt;
-    std::vector<std::unique_ptr<Pattern>> pats;
-    std::vector<void*> owned;
-    auto cleanup = [&]() {
-        batch_lt_free(ctx, blt);
-        for (auto& p : pats) free_pattern(ctx, *p);
-        for (void* p : owned) dev_free(ctx, p);
-        cudaStreamSynchronize(ctx->stream);
-    };
-#define BSTEP(call) do { ss_status _st = (call); if (_st != SS_OK) { cleanup(); return _st; } } while (0)
-    BSTEP(batch_trace_systems(ctx, Hv, ncv, Cv, opt.w, blt));
-    std::vector<int> pat_of(ns, -1), rep_sys;
+    const size_t ns = w.H.size();
+    w.t0 = now_ms();
+    w.launched = false;
+#define WSTEP(call) do { ss_status _st = (call); if (_st != SS_OK) { wave_release(w); return _st; } } while (0)
+    // (1) every system's L~ with a fixed number of launches
+    WSTEP(batch_trace_systems(ctx, w.H, w.n_c, w.C, opt.w, w.blt));
+    BatchLt& blt = w.blt;
+    // (2) distinct patterns: hash, then an exact check on the device, within
+    // the wave and against the cache
+    w.pat_of.assign(ns, -1);
+    std::vector<int> rep_sys;
+    std::vector<PatternKey> rep_key;
     {
-        std::map<std::tuple<int64_t, int64_t, int64_t, unsigned long long>, int> first;
+        std::map<PatternKey, int> first;
         std::vector<std::pair<int, int>> pairs;
         for (size_t q = 0; q < ns; ++q) {
-            auto key = std::make_tuple(blt.d[q], blt.n[q], blt.meta[q].nnz, blt.meta[q].hash);
+            const PatternKey key = std::make_tuple(blt.d[q], blt.n[q], blt.meta[q].nnz, blt.meta[q].hash);
             auto it = first.find(key);
             if (it == first.end()) {
                 first.emplace(key, (int)rep_sys.size());
-                pat_of[q] = (int)rep_sys.size();
+                w.pat_of[q] = (int)rep_sys.size();
                 rep_sys.push_back((int)q);
+                rep_key.push_back(key);
             } else {
-                pat_of[q] = it->second;
+                w.pat_of[q] = it->second;
                 pairs.emplace_back((int)q, rep_sys[it->second]);
             }
         }
         std::vector<int> mismatch;
-        BSTEP(batch_verify_patterns(ctx, blt, pairs, mismatch));
+        WSTEP(batch_verify_patterns(ctx, blt, pairs, mismatch));
         for (size_t k = 0; k < pairs.size(); ++k)
             if (mismatch[k]) {                 // equal hashes, different patterns: a pattern of its own
-                pat_of[pairs[k].first] = (int)rep_sys.size();
+                w.pat_of[pairs[k].first] = (int)rep_sys.size();
                 rep_sys.push_back(pairs[k].first);
+                rep_key.push_back(std::make_tuple(blt.d[pairs[k].first], blt.n[pairs[k].first],
+                                                  blt.meta[pairs[k].first].nnz, blt.meta[pairs[k].first].hash));
             }
     }
-    for (size_t p = 0; p < rep_sys.size(); ++p) {
-        pats.emplace_back(new Pattern());
-        pats.back()->d = blt.d[rep_sys[p]];
-        BSTEP(batch_download_pattern(ctx, blt, rep_sys[p], pats.back()->rp, pats.back()->col));
+    w.pats.assign(rep_sys.size(), nullptr);
+    if (w.cache) {
+        std::lock_guard<std::mutex> lock(w.cache->mu);
+        for (size_t p = 0; p < rep_sys.size(); ++p) {
+            auto it = w.cache->by_key.find(rep_key[p]);
+            if (it == w.cache->by_key.end()) continue;
+            for (const auto& cand : it->second) {
+                int mism = 1;
+                WSTEP(batch_verify_against(ctx, blt, rep_sys[p], cand->rp_d, cand->col_d, &mism));
+                if (!mism) {
+                    w.pats[p] = cand;
+                    w.cache->touch(rep_key[p], cand);
+                    break;
+                }
+            }
+        }
     }
-    SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    {
-        const size_t np = pats.size();
-        const size_t nth = std::max<size_t>(1, std::min<size_t>(np, std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()))));
+    std::vector<size_t> fresh;
+    for (size_t p = 0; p < rep_sys.size(); ++p)
+        if (!w.pats[p]) {
+            w.pats[p] = std::make_shared<Pattern>();
+            w.pats[p]->d = blt.d[rep_sys[p]];
+            w.pats[p]->device = ctx->device;
+            WSTEP(batch_download_pattern(ctx, blt, rep_sys[p], w.pats[p]->rp, w.pats[p]->col));
+            fresh.push_back(p);
+        }
+    if (!fresh.empty()) {
+        SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        const size_t nth = std::max<size_t>(1, std::min<size_t>(fresh.size(), std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()))));
         if (nth <= 1) {
-            for (auto& P : pats) build_pattern_host(*P, opt.use_rcm);
+            for (size_t p : fresh) build_pattern_host(*w.pats[p], opt.use_rcm);
         } else {
             std::vector<std::thread> th;
             for (size_t t = 0; t < nth; ++t)
                 th.emplace_back([&, t]() {
-                    for (size_t p = t; p < np; p += nth) build_pattern_host(*pats[p], opt.use_rcm);
+                    for (size_t k = t; k < fresh.size(); k += nth) build_pattern_host(*w.pats[fresh[k]], opt.use_rcm);
                 });
             for (auto& x : th) x.join();
         }
+        for (size_t p : fresh) {
+            Pattern& P = *w.pats[p];
+            if (P.status != SS_OK) { ss_status e = set_error(ctx, P.status, P.error); wave_release(w); return e; }
+            WSTEP(upload_pattern(ctx, P));
+        }
+        if (w.cache) {
+            // a cached pattern is used by later waves on other streams: its upload must be complete
+            SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            std::lock_guard<std::mutex> lock(w.cache->mu);
+            for (size_t p : fresh) w.cache->insert(rep_key[p], w.pats[p]);
+        }
     }
-    for (auto& P : pats) {
-        if (P->status != SS_OK) { ss_status e = set_error(ctx, P->status, P->error); cleanup(); return e; }
-        BSTEP(upload_pattern(ctx, *P));
-    }
-    // per-system buffers (one allocation) and descriptors; describe() lays
+    // (3) per-system buffers (one allocation) and descriptors; describe() lays
     // out system q's buffers from address base and returns the bytes used
     const size_t inner = mixed ? sizeof(float2) : sizeof(double2);
     auto describe = [&](size_t q, uintptr_t base, BatchSys& b, GatherEntry& g) -> size_t {
-        const Pattern& P = *pats[pat_of[q]];
+        const Pattern& P = *w.pats[w.pat_of[q]];
         const int64_t n = blt.n[q], nnz = blt.meta[q].nnz;
         size_t off = 0;
         auto take = [&](size_t sz) { uintptr_t p = base + off; off += (sz + 255) & ~size_t(255); return p; };
@@ -385,8 +392,8 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
         b.work = reinterpret_cast<void*>(take(10 * n * inner));
         b.x64 = reinterpret_cast<double2*>(take(n * sizeof(double2)));
         b.r64 = reinterpret_cast<double2*>(take(n * sizeof(double2)));
-        b.rho_out = rho_on_device ? reinterpret_cast<double2*>(rho_out[fastidx[q]])
-                                  : reinterpret_cast<double2*>(take(n * sizeof(double2)));
+        b.rho_out = w.rho_on_device ? reinterpret_cast<double2*>(w.rho_out[q])
+                                    : reinterpret_cast<double2*>(take(n * sizeof(double2)));
         auto set_op = [&](PackedOp& o, const PackedDev& dv) {
             o.meta = dv.meta;
             o.col = dv.col;
@@ -413,24 +420,22 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
         b.tidx = P.tidx_d;
         return off;
     };
-    std::vector<BatchSys> hs(ns);
+    w.hs.assign(ns, BatchSys{});
     std::vector<GatherEntry> gather(ns);
     std::vector<size_t> boff(ns + 1, 0);
-    for (size_t q = 0; q < ns; ++q) boff[q + 1] = boff[q] + describe(q, 0, hs[q], gather[q]);
+    for (size_t q = 0; q < ns; ++q) boff[q + 1] = boff[q] + describe(q, 0, w.hs[q], gather[q]);
     char* blk_all = nullptr;
-    BSTEP(dev_alloc(ctx, reinterpret_cast<void**>(&blk_all), boff[ns]));
-    owned.push_back(blk_all);
-    for (size_t q = 0; q < ns; ++q) describe(q, reinterpret_cast<uintptr_t>(blk_all) + boff[q], hs[q], gather[q]);
-    BSTEP(batch_gather_values(ctx, blt, gather));
-    BatchSys* dsys = nullptr;
-    int* ctl = nullptr;
-    BSTEP(dev_alloc_n(ctx, &dsys, hs.size()));
-    owned.push_back(dsys);
-    BSTEP(dev_alloc_n(ctx, &ctl, 4));
-    owned.push_back(ctl);
-    SS_CUDA(ctx, cudaMemcpyAsync(dsys, hs.data(), sizeof(BatchSys) * hs.size(), cudaMemcpyHostToDevice, ctx->stream));
-    SS_CUDA(ctx, cudaMemsetAsync(ctl, 0, sizeof(int) * 4, ctx->stream));
-    const double t1 = now_ms();
+    WSTEP(dev_alloc(ctx, reinterpret_cast<void**>(&blk_all), boff[ns]));
+    w.owned.push_back(blk_all);
+    for (size_t q = 0; q < ns; ++q) describe(q, reinterpret_cast<uintptr_t>(blk_all) + boff[q], w.hs[q], gather[q]);
+    WSTEP(batch_gather_values(ctx, blt, gather));
+    WSTEP(dev_alloc_n(ctx, &w.dsys, ns));
+    w.owned.push_back(w.dsys);
+    WSTEP(dev_alloc_n(ctx, &w.ctl, 4));
+    w.owned.push_back(w.ctl);
+    SS_CUDA(ctx, cudaMemcpyAsync(w.dsys, w.hs.data(), sizeof(BatchSys) * ns, cudaMemcpyHostToDevice, ctx->stream));
+    SS_CUDA(ctx, cudaMemsetAsync(w.ctl, 0, sizeof(int) * 4, ctx->stream));
+    w.t1 = now_ms();
 
     BatchParams bp;
     bp.tol = opt.tol;
@@ -442,53 +447,148 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
     // bulk copies stage the triangles' packed arrays: all must start on 16 bytes
     bp.ring_allowed = 1;
     auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-    for (const BatchSys& b : hs)
+    for (const BatchSys& b : w.hs)
         for (const PackedOp* o : {&b.lo, &b.up})
             if (!a16(o->meta) || !a16(o->col) || !a16(o->val) || (o->dinv && !a16(o->dinv))) bp.ring_allowed = 0;
     std::vector<BatchShape> shapes(ns);
     for (size_t q = 0; q < ns; ++q) {
-        const Pattern& P = *pats[pat_of[q]];
+        const Pattern& P = *w.pats[w.pat_of[q]];
         shapes[q] = BatchShape{(int32_t)blt.n[q], P.lo.nlev, P.up.nlev, P.lo.E, 32 / P.lo.G, P.up.E, 32 / P.up.G};
     }
-    BSTEP(batch_launch(ctx, dsys, (int)hs.size(), bp, shapes, ctl, ctl + 1));
-    SS_CUDA(ctx, cudaMemcpyAsync(hs.data(), dsys, sizeof(BatchSys) * hs.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    WSTEP(batch_launch(ctx, w.dsys, (int)ns, bp, shapes, w.ctl, w.ctl + 1));
+    if (w.stage_pinned) {
+        // results to pinned memory, asynchronously: [descriptors][error word][rho ...]
+        const size_t hs_bytes = (ns * sizeof(BatchSys) + 255) & ~size_t(255);
+        unsigned char* base = reinterpret_cast<unsigned char*>(w.stage);
+        SS_CUDA(ctx, cudaMemcpyAsync(base, w.dsys, sizeof(BatchSys) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+        SS_CUDA(ctx, cudaMemcpyAsync(base + hs_bytes, w.ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        w.stage_off.assign(ns, 0);
+        size_t off = hs_bytes + 256;
+        if (!w.rho_on_device)
+            for (size_t q = 0; q < ns; ++q) {
+                w.stage_off[q] = off;
+                SS_CUDA(ctx, cudaMemcpyAsync(base + off, w.hs[q].rho_out, sizeof(double2) * blt.n[q],
+                                             cudaMemcpyDeviceToHost, ctx->stream));
+                off += sizeof(double2) * blt.n[q];
+            }
+    }
+    if (!w.done) SS_CUDA(ctx, cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming));
+    SS_CUDA(ctx, cudaEventRecord(w.done, ctx->stream));
+    w.launched = true;
+#undef WSTEP
+    return SS_OK;
+}
+
+ss_status wave_end(BatchWave& w, ss_info* infos) {
+    ss_ctx ctx = w.ctx;
+    const size_t ns = w.H.size();
+    cudaError_t e = w.launched ? cudaEventSynchronize(w.done) : cudaSuccess;
     int herr = 0;
-    SS_CUDA(ctx, cudaMemcpyAsync(&herr, ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    if (!rho_on_device)
-        for (size_t q = 0; q < fastidx.size(); ++q)
-            SS_CUDA(ctx, cudaMemcpyAsync(rho_out[fastidx[q]], hs[q].rho_out, sizeof(double2) * hs[q].n,
-                                         cudaMemcpyDeviceToHost, ctx->stream));
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) { cleanup(); return cuda_check(ctx, e, "steady_state_batched"); }
-    // (the copies above read hs[q].rho_out, which the kernel does not change)
-    const double t2 = now_ms();
-    for (size_t q = 0; q < fastidx.size(); ++q) {
-        const int k = fastidx[q];
-        const Pattern& P = *pats[pat_of[q]];
-        if (herr) hs[q].status = SS_ERR_TIMEOUT;
-        if (infos) {
-            ss_info& inf = infos[k];
-            std::memset(&inf, 0, sizeof(inf));
-            inf.status = hs[q].status;
-            inf.iters = hs[q].iters;
-            inf.outer_iters = hs[q].outer;
-            inf.resid_Lrho = hs[q].resid;
-            inf.w_used = blt.w[q];
-            inf.n = hs[q].n;
-            inf.nnz = blt.meta[q].nnz;
-            inf.nnz_factors = blt.meta[q].nnz;
-            inf.levels_lower = P.n_levels;
-            inf.levels_upper = P.up_levels;
-            inf.ms_setup = (t1 - t0) / fastidx.size();
-            inf.ms_solve = (t2 - t1) / fastidx.size();
-        }
-        if (hs[q].status != SS_OK) {
-            if (hs[q].status != SS_NOT_CONVERGED && hs[q].status != SS_BREAKDOWN) worst = (ss_status)hs[q].status;
-            else if (worst == SS_OK) worst = (ss_status)hs[q].status;
+    if (e == cudaSuccess) {
+        if (w.stage_pinned) {
+            const unsigned char* base = reinterpret_cast<const unsigned char*>(w.stage);
+            const size_t hs_bytes = (ns * sizeof(BatchSys) + 255) & ~size_t(255);
+            std::memcpy(w.hs.data(), base, sizeof(BatchSys) * ns);
+            std::memcpy(&herr, base + hs_bytes, sizeof(int));
+            if (!w.rho_on_device)
+                for (size_t q = 0; q < ns; ++q)
+                    std::memcpy(w.rho_out[q], base + w.stage_off[q], sizeof(double2) * w.blt.n[q]);
+        } else {
+            e = cudaMemcpyAsync(w.hs.data(), w.dsys, sizeof(BatchSys) * ns, cudaMemcpyDeviceToHost, ctx->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&herr, w.ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+            if (!w.rho_on_device)
+                for (size_t q = 0; q < ns && e == cudaSuccess; ++q)
+                    e = cudaMemcpyAsync(w.rho_out[q], w.hs[q].rho_out, sizeof(double2) * w.blt.n[q],
+                                        cudaMemcpyDeviceToHost, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         }
     }
-    cleanup();
-#undef BSTEP
+    if (e != cudaSuccess) {
+        wave_release(w);
+        return cuda_check(ctx, e, "steady_state_batched");
+    }
+    w.t2 = now_ms();
+    ss_status worst = SS_OK;
+    for (size_t q = 0; q < ns; ++q) {
+        const Pattern& P = *w.pats[w.pat_of[q]];
+        if (herr) w.hs[q].status = SS_ERR_TIMEOUT;
+        if (infos) {
+            ss_info& inf = infos[q];
+            std::memset(&inf, 0, sizeof(inf));
+            inf.status = w.hs[q].status;
+            inf.iters = w.hs[q].iters;
+            inf.outer_iters = w.hs[q].outer;
+            inf.resid_Lrho = w.hs[q].resid;
+            inf.w_used = w.blt.w[q];
+            inf.n = w.hs[q].n;
+            inf.nnz = w.blt.meta[q].nnz;
+            inf.nnz_factors = w.blt.meta[q].nnz;
+            inf.levels_lower = P.n_levels;
+            inf.levels_upper = P.up_levels;
+            inf.ms_setup = (w.t1 - w.t0) / ns;
+            inf.ms_solve = (w.t2 - w.t1) / ns;
+        }
+        if (w.hs[q].status != SS_OK) {
+            if (w.hs[q].status != SS_NOT_CONVERGED && w.hs[q].status != SS_BREAKDOWN) worst = (ss_status)w.hs[q].status;
+            else if (worst == SS_OK) worst = (ss_status)w.hs[q].status;
+        }
+    }
+    wave_release(w);
+    if (worst != SS_OK) ctx->last_error = "at least one system did not converge (see infos)";
+    return worst;
+}
+
+extern "C" ss_status steady_state(ss_ctx, const ss_csr_view*, int, const ss_csr_view*, const ss_options*, double*, int,
+                                  ss_info*);
+
+extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_view* H, const int* n_c,
+                                          const ss_csr_view* const* c_ops, const ss_options* opt_in,
+                                          double* const* rho_out, int rho_on_device, ss_info* infos) {
+    if (!ctx) return SS_ERR_INVALID;
+    SS_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (n_sys < 0 || (n_sys > 0 && (!H || !n_c || !rho_out))) return set_error(ctx, SS_ERR_INVALID, "null argument");
+    ss_options opt;
+    ss_options_default(&opt);
+    if (opt_in) opt = *opt_in;
+    const bool mixed = opt.precision == SS_PREC_MIXED;
+    const bool fast = opt.method == SS_METHOD_ITER_BICGSTAB && opt.precond == SS_PRECOND_ILU0;
+    const int max_n_fast = batch_max_n(mixed);
+    std::vector<int> slow;
+    std::vector<int> fastidx;
+    for (int k = 0; k < n_sys; ++k) {
+        const int64_t d = H[k].n_rows;
+        if (fast && d > 0 && d * d <= max_n_fast) fastidx.push_back(k);
+        else slow.push_back(k);
+    }
+    // systems outside the persistent kernel's scope: the single-system path
+    ss_status worst = SS_OK;
+    for (int k : slow) {
+        ss_info inf{};
+        ss_status st = steady_state(ctx, &H[k], n_c[k], n_c[k] ? c_ops[k] : nullptr, &opt, rho_out[k],
+                                    rho_on_device, &inf);
+        if (infos) infos[k] = inf;
+        if (st != SS_OK && st != SS_NOT_CONVERGED && st != SS_BREAKDOWN) return st;
+        if (st != SS_OK) worst = st;
+    }
+    if (fastidx.empty()) return worst;
+    BatchWave w;
+    w.ctx = ctx;
+    w.opt = opt;
+    w.rho_on_device = rho_on_device;
+    for (int k : fastidx) {
+        w.H.push_back(&H[k]);
+        w.n_c.push_back(n_c[k]);
+        w.C.push_back(n_c[k] ? c_ops[k] : nullptr);
+        w.rho_out.push_back(rho_out[k]);
+    }
+    SS_TRY(wave_begin(w));
+    std::vector<ss_info> winf(fastidx.size());
+    ss_status st = wave_end(w, winf.data());
+    if (infos)
+        for (size_t q = 0; q < fastidx.size(); ++q) infos[fastidx[q]] = winf[q];
+    if (st != SS_OK && st != SS_NOT_CONVERGED && st != SS_BREAKDOWN) return st;
+    if (st != SS_OK && worst == SS_OK) worst = st;
     if (worst != SS_OK) ctx->last_error = "at least one system did not converge (see infos)";
     return worst;
 }

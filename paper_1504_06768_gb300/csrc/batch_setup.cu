@@ -230,6 +230,19 @@ __global__ void pattern_verify_b(const int2* __restrict__ pairs, const int32_t* 
     if (bad) atomicOr(&mismatch[blockIdx.y], 1);
 }
 
+// System s's pattern against a pattern held elsewhere on the device.
+__global__ void pattern_compare(const int32_t* __restrict__ ra, const int32_t* __restrict__ ca,
+                                const int32_t* __restrict__ rb, const int32_t* __restrict__ cb, int64_t n,
+                                int64_t nnz, int* __restrict__ mismatch) {
+    bool bad = false;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n + 1 || t < nnz;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < n + 1 && ra[t] != rb[t]) bad = true;
+        if (t < nnz && ca[t] != cb[t]) bad = true;
+    }
+    if (bad) atomicOr(mismatch, 1);
+}
+
 // --------------------------------------------------------- gather
 
 __global__ void gather_values_b(const GatherEntry* __restrict__ tab, const double2* __restrict__ val) {
@@ -488,5 +501,24 @@ ss_status batch_gather_values(ss_ctx ctx, const BatchLt& b, const std::vector<Ga
     }
     dev_free(ctx, td);
     if (ce != cudaSuccess) return cuda_check(ctx, ce, "value gather");
+    return SS_OK;
+}
+
+ss_status batch_verify_against(ss_ctx ctx, const BatchLt& b, int s, const int32_t* rp_d, const int32_t* col_d,
+                               int* mismatch) {
+    *mismatch = 1;
+    int* md = nullptr;
+    SS_TRY(dev_alloc_n(ctx, &md, 1));
+    const int64_t n = b.n[s], nnz = b.meta[s].nnz;
+    cudaError_t ce = cudaMemsetAsync(md, 0, sizeof(int), ctx->stream);
+    if (ce == cudaSuccess) {
+        pattern_compare<<<(ss_count_launch(), std::min<unsigned>(grid_for(std::max(n + 1, nnz), 256), 128u)), 256, 0,
+                           ctx->stream>>>(b.rp + b.row_off[s] + s, b.col + b.meta[s].nz_off, rp_d, col_d, n, nnz, md);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(mismatch, md, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, md);
+    if (ce != cudaSuccess) return cuda_check(ctx, ce, "pattern verification");
     return SS_OK;
 }

@@ -129,6 +129,10 @@ ss_status batch_verify_patterns(ss_ctx ctx, const BatchLt& b, const std::vector<
 ss_status batch_download_pattern(ss_ctx ctx, const BatchLt& b, int s, std::vector<int32_t>& rp,
                                  std::vector<int32_t>& col);
 ss_status batch_gather_values(ss_ctx ctx, const BatchLt& b, const std::vector<GatherEntry>& tab);
+// *mismatch = 1 unless system s's pattern equals the natural-order pattern
+// (rp_d: n + 1 row pointers, col_d: nnz columns) on the device.
+ss_status batch_verify_against(ss_ctx ctx, const BatchLt& b, int s, const int32_t* rp_d, const int32_t* col_d,
+                               int* mismatch);
 
 int batch_max_n(bool mixed);
 // Chooses the shared-memory plan (ring size, level boundaries in shared

@@ -23,9 +23,14 @@ template <> struct SpmvOps<float2> {
     }
 };
 
-// y[i] = sum_t A[i, col[t]] x[col[t]]; G lanes per row.  `halt` (may be null)
-// lets a solver skip launches it has already queued once it has converged.
-template <int G, class V, class T>
+// y[i] = sum_t A[i, col[t]] x[col[t]]; G lanes per row.  Each lane issues the
+// column and value loads of its next K entries before it gathers x and
+// before any arithmetic, so a row costs two dependent memory round trips
+// whatever its length up to K G.  Columns and values are streamed past L1
+// (read once); x is gathered through the read-only cache.  `halt` (may be
+// null) lets a solver skip launches it has already queued once it has
+// converged.
+template <int G, int K, class V, class T>
 __global__ void __launch_bounds__(256) spmv_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                    const V* __restrict__ val, int64_t n, const T* __restrict__ x,
                                                    T* __restrict__ y, const int* __restrict__ halt) {
@@ -36,7 +41,21 @@ __global__ void __launch_bounds__(256) spmv_kernel(const int32_t* __restrict__ r
     T acc = SpmvOps<T>::zero();
     if (row < n) {
         const int32_t a = rp[row], b = rp[row + 1];
-        for (int32_t t = a + sub; t < b; t += G) acc = SpmvOps<T>::madd(val[t], __ldg(&x[col[t]]), acc);
+        for (int32_t base = a + sub; base < b; base += K * G) {
+            int32_t c[K];
+            V v[K];
+            T xv[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int32_t t = base + k * G;
+                c[k] = t < b ? __ldcs(&col[t]) : -1;
+                v[k] = t < b ? __ldcs(&val[t]) : V{};
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) xv[k] = c[k] >= 0 ? __ldg(&x[c[k]]) : SpmvOps<T>::zero();
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = SpmvOps<T>::madd(v[k], xv[k], acc);
+        }
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
@@ -47,7 +66,9 @@ __global__ void __launch_bounds__(256) spmv_kernel(const int32_t* __restrict__ r
     if (row < n && sub == 0) y[row] = acc;
 }
 
-int spmv_group_size(int64_t n_rows, int64_t nnz);
+// Lanes per row for a mean row length (FP64: the FP64 pipe is the scarce unit,
+// fewer lanes per row; FP32: more lanes, more loads in flight).
+int spmv_group_size(int64_t n_rows, int64_t nnz, bool fp32);
 void spmv_launch(const DeviceCSR& A, const double2* x, double2* y, const int* halt, cudaStream_t s);
 void spmv_launch32(const DeviceCSR& A, const float2* val32, const float2* x, float2* y, const int* halt,
                    cudaStream_t s);
