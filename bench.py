@@ -2,9 +2,10 @@
 workload (cavity cutoff 40 x two-level atom, Hilbert dimension 80, a
 6400 x 6400 complex Liouvillian), at ||L rho||_2 <= 1e-10.
 
-One step = one batch of S systems (default S = 152, one per SM; seeds
-rank*S .. rank*S+S-1, drive E ~ U[0.2, 1.5]) taken through the whole path on
-the GPU by steady_state_batched: Kronecker assembly of L, trace row of
+One step = one batch of S systems (default S = 608, four per SM, so that the
+persistent kernel's work queue evens out the systems' uneven iteration
+counts; seeds rank*S .. rank*S+S-1, drive E ~ U[0.2, 1.5]) taken through the
+whole path on the GPU by steady_state_batched: Kronecker assembly of L, trace row of
 Eq. (linear), RCM ordering, iLU(0), preconditioned BiCGSTAB, acceptance test
 ||L rho||_2 <= 1e-10 and trace-normalised rho.  The headline precision is the
 FP32-inner / FP64-refined path; the same step in FP64 is timed after it
@@ -39,7 +40,8 @@ if ROOT not in sys.path:
 METRIC = "steady-state solves/s at ||L rho||<=1e-10"
 UNIT = "solves/s"
 TOL = 1e-10
-BATCH = 152          # systems per step: one per SM of a GB300 (seeds rank*BATCH ...)
+BATCH = 608          # systems per step: four per SM of a GB300, so that the persistent kernel's
+                     # work queue balances systems of uneven iteration counts (seeds rank*BATCH ...)
 JC_N = 40
 
 
@@ -327,7 +329,8 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "c64 inner / c128 refined" if args.precision == "mixed" else "c128 (f64)",
         "data": "synthetic",
         "config": {"workload": "jc40: driven dissipative Jaynes-Cummings, cavity 40 x atom, n=6400, "
-                               f"{BATCH} seeds per step (E~U[0.2,1.5]), one persistent launch per step",
+                               f"{BATCH} seeds per step (E~U[0.2,1.5]), one persistent launch per step "
+                               "(one CTA per SM takes systems from a queue)",
                    "method": args.method, "precond": precond, "precision": args.precision, "ordering": "rcm",
                    "tol": TOL,
                    "batch_per_gpu": BATCH, "parallelism": f"replicas x{ws}",
@@ -344,12 +347,100 @@ def run_gpu(args):
                   "ms_setup_mean": statistics.mean(i["ms_setup"] for i in step_infos),
                   "ms_solve_mean": statistics.mean(i["ms_solve"] for i in step_infos)},
     }
+    if rank == 0 and not args.no_spmv:
+        out["spmv"] = spmv_measure(ss, B, ctx, stream)
+    if rank == 0 and not args.no_serve:
+        out["serving"] = serve_measure(ss, args)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return out if rank == 0 else None
+
+
+# ------------------------------------------------ SpMV roofline and serving
+
+def spmv_measure(ss, B, ctx, stream, reps: int = 20):
+    """SpMV of the RCM-ordered trace-row Liouvillian of the 3-site Kerr chain
+    (cutoff 12 per site: n = 2,985,984, nnz = 41.5M, far larger than L2) in
+    FP64 and FP32, timed with CUDA events on the solver's stream.  Bytes: the
+    CSR once (values + int32 columns + row pointers) and x, y once each."""
+    import ctypes as C
+    import torch
+    from workloads import kerr_chain
+    s = kerr_chain()
+    A, _ = ss.add_trace_row(ss.assemble_liouvillian(s.H, s.c_ops))
+    perm, _, _ = ss.rcm_permute(A)
+    Ap = ss.permute(A, perm)
+    n, nnz = Ap.shape[0], Ap.nnz
+    lib = B.load()
+    x = torch.randn(n, dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    x32 = x.to(torch.complex64)
+    y32 = torch.empty_like(x32)
+    peak, kind = _peaks()
+    res = {"matrix": "3-site Kerr chain trace-row Liouvillian, RCM order", "n": n, "nnz": nnz}
+    for name, fn, vb in (("fp64", lambda: lib.spmv(ctx.handle, Ap.handle, C.c_void_p(x.data_ptr()),
+                                                    C.c_void_p(y.data_ptr())), 16),
+                         ("fp32", lambda: lib.spmv_f32(ctx.handle, Ap.handle, C.c_void_p(x32.data_ptr()),
+                                                        C.c_void_p(y32.data_ptr())), 8)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        bytes_ = nnz * (vb + 4) + (n + 1) * 4 + 2 * n * vb
+        gbs = bytes_ / (ms / 1000.0) / 1e9
+        res[name] = {"us": 1000.0 * ms, "bytes": bytes_, "GB/s": gbs, "frac_hbm": gbs / peak,
+                     "peak_source": kind}
+    # FP64 complex SpMV does 4 DFMA per stored entry; GB300 runs FP64 FMA at
+    # about 1.26 TFLOP/s (measured), so that form is bound by the FP64 pipe
+    res["fp64"]["fp64_tflops"] = 8.0 * nnz / (res["fp64"]["us"] * 1e-6) / 1e12
+    return res
+
+
+def serve_measure(ss, args):
+    """A Poisson stream (seeded) of JC40 and Kerr-sweep requests through the
+    serving loop; latency from submission to completion per request."""
+    import numpy as np
+    from workloads import jaynes_cummings_rwa, kerr_sweep
+    rng = np.random.default_rng(0)
+    n_req, rate = args.serve_requests, args.serve_rate
+    pool = [jaynes_cummings_rwa(seed=1000 + k, N=JC_N) for k in range(32)] + kerr_sweep(96, seed=7)
+    pick = rng.integers(0, len(pool), size=n_req)
+    gaps = rng.exponential(1.0 / rate, size=n_req)
+    with ss.Server(precision=args.precision, tol=TOL) as srv:
+        # warm: one request of each pattern class through the loop
+        for t in [srv.submit(pool[0].H, pool[0].c_ops), srv.submit(pool[40].H, pool[40].c_ops)]:
+            srv.wait(t, timeout_s=300)
+        t0 = time.perf_counter()
+        tickets = []
+        due = t0
+        for k in range(n_req):
+            due += gaps[k]
+            delay = due - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            sysm = pool[pick[k]]
+            tickets.append(srv.submit(sysm.H, sysm.c_ops))
+        lat, ok = [], 0
+        for t in tickets:
+            _, info, ms = srv.wait(t, timeout_s=600, raise_on_failure=False)
+            lat.append(ms)
+            ok += info["status"] == 0 and info["resid_Lrho"] <= TOL
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+    lat = np.array(lat)
+    return {"requests": n_req, "rate_per_s": rate, "mix": "JC40 (n=6400) and Kerr N~U{8..64}",
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "solves_per_s": n_req / wall, "converged": int(ok),
+            "waves": stats["waves"], "precision": args.precision}
 
 
 # ----------------------------------------------------------- CPU (oracle) arm
@@ -417,6 +508,10 @@ def main():
     ap.add_argument("--precond", default="ilu0", choices=["ilu0", "ilut"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--no-spmv", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-rate", type=float, default=300.0)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")

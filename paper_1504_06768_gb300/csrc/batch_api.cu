@@ -453,7 +453,10 @@ ss_status wave_begin(BatchWave& w) {
     std::vector<BatchShape> shapes(ns);
     for (size_t q = 0; q < ns; ++q) {
         const Pattern& P = *w.pats[w.pat_of[q]];
-        shapes[q] = BatchShape{(int32_t)blt.n[q], P.lo.nlev, P.up.nlev, P.lo.E, 32 / P.lo.G, P.up.E, 32 / P.up.G};
+        int32_t wide = 1;
+        for (const std::vector<int32_t>* lv : {&P.hl.lvl, &P.hu.lvl})
+            for (size_t l = 0; l + 1 < lv->size(); ++l) wide = std::max(wide, (*lv)[l + 1] - (*lv)[l]);
+        shapes[q] = BatchShape{(int32_t)blt.n[q], P.lo.nlev, P.up.nlev, P.lo.E, 32 / P.lo.G, P.up.E, 32 / P.up.G, wide};
     }
     WSTEP(batch_launch(ctx, w.dsys, (int)ns, bp, shapes, w.ctl, w.ctl + 1));
     if (w.stage_pinned) {

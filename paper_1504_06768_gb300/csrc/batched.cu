@@ -103,7 +103,7 @@ __device__ __forceinline__ bool negligible(double2 a, double nu, double nv) {
 
 // ------------------------------------------------------ triangular solves
 constexpr int MAXE = BATCH_MAXE;    // packed entries per lane and unit
-constexpr int RING = BATCH_RING;    // shared-memory slots of the level ring (RING - 1 levels in flight)
+constexpr int RING_MAX = BATCH_RING_MAX;    // shared-memory slots of the level ring, at most
 
 // One unit of a packed operand held in registers (a lane's slots, the row
 // and its CSR tail).
@@ -169,20 +169,22 @@ __device__ __forceinline__ void solve_row(const UnitRegs<T>& cu, T dinv, const i
 
 // Shared-memory ring that stages the packed units of the next levels of a
 // triangular solve with bulk asynchronous copies (TMA), so that the data of a
-// level was requested RING - 1 levels earlier and the critical path of a
+// level was requested nslots - 1 levels earlier and the critical path of a
 // level is shared-memory latency, the arithmetic and one barrier.  One thread
 // issues a level's copies (values, columns, row records, inverse diagonal)
 // into a slot and arms the slot's mbarrier with their byte count; every
 // thread waits on the mbarrier's phase before reading the slot.  Levels are
-// numbered across calls (seq), slot = seq mod RING, phase parity =
-// (seq / RING) mod 2.
+// numbered across calls (seq), slot = seq mod nslots, phase parity =
+// (seq / nslots) mod 2.
 struct Ring {
     unsigned char* base;
-    uint64_t* bars;                 // RING mbarriers (shared)
+    uint64_t* bars;                 // nslots "full" mbarriers: the slot's copies have landed (shared)
+    uint64_t* empty;                // nslots "empty" mbarriers: the slot's level has been solved (shared)
     int* abort;                     // shared flag: a wait ran out of time
     int* err;                       // global error word
     int32_t slot_bytes;
     int32_t umax;                   // units per staged level (0: no ring)
+    int32_t nslots;                 // slots (2 .. RING_MAX)
     uint32_t seq;                   // levels staged so far by this block
 };
 
@@ -209,6 +211,12 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)_
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void named_barrier(int id, int threads) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(threads) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
@@ -237,12 +245,13 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 
 constexpr uint64_t RING_WAIT_NS = 2000000000ull;   // 2 s: far beyond any copy; only a fault ends there
 
-// Wait for the phase of a slot; after RING_WAIT_NS the block gives up, raises
-// the error word and the abort flag, and later waits return at once.
-__device__ __forceinline__ void ring_wait(const Ring& rg, int slot, unsigned parity) {
-    if (mbar_try_wait(rg.bars + slot, parity)) return;
+// Wait for a phase of one of the ring's mbarriers; after RING_WAIT_NS the
+// block gives up, raises the error word and the abort flag, and later waits
+// return at once.
+__device__ __forceinline__ void ring_wait_on(const Ring& rg, uint64_t* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return;
     const uint64_t t0 = globaltimer_ns();
-    while (!mbar_try_wait(rg.bars + slot, parity)) {
+    while (!mbar_try_wait(bar, parity)) {
         if (*(volatile int*)rg.abort) return;
         if (globaltimer_ns() - t0 > RING_WAIT_NS) {
             *(volatile int*)rg.abort = 1;
@@ -250,6 +259,10 @@ __device__ __forceinline__ void ring_wait(const Ring& rg, int slot, unsigned par
             return;
         }
     }
+}
+
+__device__ __forceinline__ void ring_wait(const Ring& rg, int slot, unsigned parity) {
+    ring_wait_on(rg, rg.bars + slot, parity);
 }
 
 // One thread: copies of the first min(units, umax) units of level L into slot.
@@ -280,6 +293,12 @@ __device__ __forceinline__ void stage_level(const PackedOp& P, const int32_t* lv
 // units of a level are spread over the warps and a barrier separates levels,
 // so every dependency of a row is complete when its level starts and nothing
 // waits on a flag.  lvl: first unit of each level (nlev + 1 entries).
+// Warp specialisation: the last warp only stages levels into the ring (it
+// runs ahead until every slot is full, refilling a slot once its level has
+// been solved); the other NW - 1 warps solve, separated per level by a named
+// barrier that the staging warp does not join.
+constexpr int CONSUMERS = (NW - 1) * 32;
+
 template <bool LOWER, int G, class T>
 __device__ void cta_trsv_ring(const PackedOp& P, const int32_t* lvl, const int32_t* __restrict__ ocol,
                               const T* __restrict__ oval, const T* __restrict__ inv, T* buf, Ring& rg) {
@@ -289,41 +308,51 @@ __device__ void cta_trsv_ring(const PackedOp& P, const int32_t* lvl, const int32
     const int32_t nlev = P.nlev;
     const SlotLayout sl = slot_layout<T>(E, R, umax);
     const uint32_t s0 = rg.seq;
+    const int ns = rg.nslots;
     const int dstride = dinv_stride<T>(R) / (int)sizeof(T);
-    if (threadIdx.x == 0)
-        for (int32_t L = 0; L < RING - 1 && L < nlev; ++L) stage_level<LOWER, G, T>(P, lvl, L, rg, (s0 + L) % RING, sl);
-    for (int32_t l = 0; l < nlev; ++l) {
-        if (threadIdx.x == 0 && l + RING - 1 < nlev)
-            stage_level<LOWER, G, T>(P, lvl, l + RING - 1, rg, (s0 + l + RING - 1) % RING, sl);
-        const uint32_t q = s0 + l;
-        const int slot = q % RING;
-        ring_wait(rg, slot, (q / RING) & 1u);
-        const unsigned char* sb = rg.base + (size_t)slot * rg.slot_bytes;
-        const int32_t beg = lvl[l], cnt = lvl[l + 1] - beg;
-        for (int32_t u = warp; u < cnt; u += NW) {
-            UnitRegs<T> cu;
-            T dinv = zero<T>();
-            if (u < umax) {
-                const T* sv = reinterpret_cast<const T*>(sb);
-                const int32_t* sc = reinterpret_cast<const int32_t*>(sb + sl.col);
-                const int4 m = reinterpret_cast<const int4*>(sb + sl.meta)[u * R + grp];
-#pragma unroll
-                for (int q2 = 0; q2 < MAXE; ++q2) {
-                    cu.jj[q2] = q2 < E ? sc[(u * E + q2) * 32 + lane] : -1;
-                    cu.vv[q2] = q2 < E ? sv[(u * E + q2) * 32 + lane] : zero<T>();
-                }
-                cu.i = m.x;
-                cu.ob = m.y;
-                cu.oe = m.z;
-                if (!LOWER) dinv = reinterpret_cast<const T*>(sb + sl.dinv)[u * dstride + grp];
-            } else {
-                load_unit<G, T>(P, beg + u, lane, cu);
-                if (!LOWER && cu.i >= 0) dinv = inv[cu.i];
+    if (warp == NW - 1) {
+        if (lane == 0)
+            for (int32_t L = 0; L < nlev; ++L) {
+                const uint32_t q = s0 + L;
+                // before its next use, the slot's previous level must be solved
+                if (q >= (uint32_t)ns) ring_wait_on(rg, rg.empty + q % ns, ((q / ns) + 1u) & 1u);
+                stage_level<LOWER, G, T>(P, lvl, L, rg, q % ns, sl);
             }
-            solve_row<LOWER, G, T>(cu, dinv, ocol, oval, buf, sub);
+        __syncwarp();
+    } else {
+        for (int32_t l = 0; l < nlev; ++l) {
+            const uint32_t q = s0 + l;
+            const int slot = q % ns;
+            const int32_t beg = lvl[l], cnt = lvl[l + 1] - beg;
+            if (warp < cnt) ring_wait(rg, slot, (q / ns) & 1u);        // warps without a unit do not read the slot
+            const unsigned char* sb = rg.base + (size_t)slot * rg.slot_bytes;
+            for (int32_t u = warp; u < cnt; u += NW - 1) {
+                UnitRegs<T> cu;
+                T dinv = zero<T>();
+                if (u < umax) {
+                    const T* sv = reinterpret_cast<const T*>(sb);
+                    const int32_t* sc = reinterpret_cast<const int32_t*>(sb + sl.col);
+                    const int4 m = reinterpret_cast<const int4*>(sb + sl.meta)[u * R + grp];
+#pragma unroll
+                    for (int q2 = 0; q2 < MAXE; ++q2) {
+                        cu.jj[q2] = q2 < E ? sc[(u * E + q2) * 32 + lane] : -1;
+                        cu.vv[q2] = q2 < E ? sv[(u * E + q2) * 32 + lane] : zero<T>();
+                    }
+                    cu.i = m.x;
+                    cu.ob = m.y;
+                    cu.oe = m.z;
+                    if (!LOWER) dinv = reinterpret_cast<const T*>(sb + sl.dinv)[u * dstride + grp];
+                } else {
+                    load_unit<G, T>(P, beg + u, lane, cu);
+                    if (!LOWER && cu.i >= 0) dinv = inv[cu.i];
+                }
+                solve_row<LOWER, G, T>(cu, dinv, ocol, oval, buf, sub);
+            }
+            named_barrier(1, CONSUMERS);
+            if (threadIdx.x == 0) mbar_arrive(rg.empty + slot);      // the slot may be refilled
         }
-        __syncthreads();
     }
+    __syncthreads();
     rg.seq = s0 + (uint32_t)nlev;
 }
 
@@ -331,11 +360,11 @@ __device__ void cta_trsv_ring(const PackedOp& P, const int32_t* lvl, const int32
 // for the copies still in flight into the ring.
 __device__ void ring_drain(const Ring& rg) {
     if (threadIdx.x != 0 || rg.umax == 0 || !*(volatile int*)rg.abort) return;
-    for (int k = 1; k <= RING; ++k) {
+    for (int k = 1; k <= rg.nslots; ++k) {
         if (rg.seq < (uint32_t)k) break;
         const uint32_t q = rg.seq - k;
         const uint64_t t0 = globaltimer_ns();
-        while (!mbar_try_wait(rg.bars + q % RING, (q / RING) & 1u))
+        while (!mbar_try_wait(rg.bars + q % rg.nslots, (q / rg.nslots) & 1u))
             if (globaltimer_ns() - t0 > RING_WAIT_NS) break;
     }
 }
@@ -391,6 +420,8 @@ __device__ void cta_trsv(const PackedOp& P, const int32_t* lvl, const int32_t* o
 // given.
 constexpr int SPMV_UNROLL = 4;   // units a warp loads before it consumes any
 constexpr int VU = 2;            // vector elements a thread loads before it computes
+constexpr int MU = 2;            // the same for the FP32 passes that read two or three vectors
+constexpr int MU2 = 1;           // and for the FP32 pass that reads six
 
 template <int G, class T, class A>
 __device__ void cta_spmv_pk(const PackedOp& P, const int32_t* __restrict__ ocol, const T* __restrict__ oval,
@@ -486,6 +517,7 @@ struct Ctx {
 // boundaries of both triangles (when they fit) and the level ring.
 struct SmemPlan {
     unsigned char* buf;
+    unsigned char* pbuf;        // mixed precision: p^ (null: kept in global memory)
     const int32_t* lvl_lo;
     const int32_t* lvl_up;
     Ring ring;
@@ -501,6 +533,18 @@ __device__ void cta_prec(Ctx<T>& c, const T* in, T* out) {
     cta_trsv<false, T>(S.up, c.lvl_up, S.f_col, c.fval, c.finv, c.buf, *c.ring);
     for (int32_t i = threadIdx.x; i < c.n; i += BT) out[i] = c.buf[i];
     // no barrier needed: the shared buffer is only read afterwards
+}
+
+// M^{-1} applied in place to the shared buffer, which the caller has filled
+// (and synchronised); the result stays there and is also copied to out when
+// out is not null (out may be shared or global memory).
+template <class T>
+__device__ void cta_prec_staged(Ctx<T>& c, T* out) {
+    const BatchSys& S = *c.S;
+    cta_trsv<true, T>(S.lo, c.lvl_lo, S.f_col, c.fval, c.finv, c.buf, *c.ring);
+    cta_trsv<false, T>(S.up, c.lvl_up, S.f_col, c.fval, c.finv, c.buf, *c.ring);
+    if (out)
+        for (int32_t i = threadIdx.x; i < c.n; i += BT) out[i] = c.buf[i];
 }
 
 struct KResult {
@@ -873,6 +917,7 @@ __device__ void solve_mixed(BatchSys& S, const BatchParams& P, SmemPlan& sm, dou
     T* phat = t + n;
     T* shat = phat + n;
     T* xd = shat + n;            // FP32 increment of x since the last replacement
+    T* ph = sm.pbuf ? reinterpret_cast<T*>(sm.pbuf) : phat;     // p^: shared memory when it fits
     double2* x = S.x64;
     double2* r64 = S.r64;
     for (int32_t i = threadIdx.x; i < n; i += BT) {
@@ -906,13 +951,31 @@ __device__ void solve_mixed(BatchSys& S, const BatchParams& P, SmemPlan& sm, dou
         bool restart = false;
         for (int k = 1; it < P.maxiter; ++k) {
             ++it;
-            {   // p = r + beta (p - omega v)
+            {   // p = r + beta (p - omega v), written to p and to the solve buffer
                 const T bt = cvt<T>(beta), om = cvt<T>(omega);
-                for (int32_t i = threadIdx.x; i < n; i += BT)
-                    p[i] = (k == 1) ? r[i] : addc(r[i], mulc(bt, subc(p[i], mulc(om, v[i]))));
+                for (int32_t i0 = threadIdx.x; i0 < n; i0 += MU * BT) {
+                    T ra[MU], pa[MU], va[MU];
+#pragma unroll
+                    for (int u = 0; u < MU; ++u) {
+                        const int32_t i = i0 + u * BT;
+                        if (i < n) {
+                            ra[u] = r[i];
+                            if (k > 1) { pa[u] = p[i]; va[u] = v[i]; }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < MU; ++u) {
+                        const int32_t i = i0 + u * BT;
+                        if (i < n) {
+                            const T pi = (k == 1) ? ra[u] : addc(ra[u], mulc(bt, subc(pa[u], mulc(om, va[u]))));
+                            p[i] = pi;
+                            c.buf[i] = pi;
+                        }
+                    }
+                }
             }
             __syncthreads();
-            cta_prec<T>(c, p, phat);
+            cta_prec_staged<T>(c, ph);          // p^ = M^{-1} p, kept in ph
             A dv[3] = {0, 0, 0};
             cta_spmv<T>(S.pa, S.a_col, c.aval, c.buf, v, rhat, dv);
             double dvs[3];
@@ -920,38 +983,77 @@ __device__ void solve_mixed(BatchSys& S, const BatchParams& P, SmemPlan& sm, dou
             const double2 rv = make_double2(dvs[0], dvs[1]);
             if (negligible(rv, rhat_norm, sqrt(dvs[2]))) { restart = true; break; }
             alpha = cdiv(rho, rv);
-            A ns[1] = {0};
-            {
+            {   // s = r - alpha v, written to s and to the solve buffer
                 const T al = cvt<T>(alpha);
-                for (int32_t i = threadIdx.x; i < n; i += BT) {
-                    T si = subc(r[i], mulc(al, v[i]));
-                    s[i] = si;
-                    ns[0] += norm2<T, A>(si);
+                for (int32_t i0 = threadIdx.x; i0 < n; i0 += MU * BT) {
+                    T ra[MU], va[MU];
+#pragma unroll
+                    for (int u = 0; u < MU; ++u) {
+                        const int32_t i = i0 + u * BT;
+                        if (i < n) { ra[u] = r[i]; va[u] = v[i]; }
+                    }
+#pragma unroll
+                    for (int u = 0; u < MU; ++u) {
+                        const int32_t i = i0 + u * BT;
+                        if (i < n) {
+                            const T si = subc(ra[u], mulc(al, va[u]));
+                            s[i] = si;
+                            c.buf[i] = si;
+                        }
+                    }
                 }
             }
-            double nss[1];
-            cta_sum<1, A>(ns, nss, c.red);
-            cta_prec<T>(c, s, shat);
-            A dt[3] = {0, 0, 0};
-            cta_spmv<T>(S.pa, S.a_col, c.aval, c.buf, t, nullptr, dt);
+            __syncthreads();
+            cta_prec_staged<T>(c, nullptr);     // s^ = M^{-1} s stays in the solve buffer
+            A dz[3] = {0, 0, 0};
+            cta_spmv<T>(S.pa, S.a_col, c.aval, c.buf, t, nullptr, dz);     // t = A s^
             __syncthreads();
             A tsd[3] = {0, 0, 0};
-            for (int32_t i = threadIdx.x; i < n; i += BT) {
-                acc_dot<T, A>(t[i], s[i], tsd[0], tsd[1]);
-                tsd[2] += norm2<T, A>(t[i]);
+            for (int32_t i0 = threadIdx.x; i0 < n; i0 += MU * BT) {
+                T ta[MU], sa[MU];
+#pragma unroll
+                for (int u = 0; u < MU; ++u) {
+                    const int32_t i = i0 + u * BT;
+                    if (i < n) { ta[u] = t[i]; sa[u] = s[i]; }
+                }
+#pragma unroll
+                for (int u = 0; u < MU; ++u)
+                    if (i0 + u * BT < n) {
+                        acc_dot<T, A>(ta[u], sa[u], tsd[0], tsd[1]);
+                        tsd[2] += norm2<T, A>(ta[u]);
+                    }
             }
             double tss[3];
             cta_sum<3, A>(tsd, tss, c.red);
             omega = tss[2] > 0.0 ? make_double2(tss[0] / tss[2], tss[1] / tss[2]) : make_double2(0.0, 0.0);
             A nr2[3] = {0, 0, 0};
-            {
+            {   // xd += alpha p^ + omega s^, r = s - omega t, with (r^, r) and |r|^2
                 const T al = cvt<T>(alpha), om = cvt<T>(omega);
-                for (int32_t i = threadIdx.x; i < n; i += BT) {
-                    xd[i] = addc(xd[i], addc(mulc(al, phat[i]), mulc(om, shat[i])));
-                    T ri = subc(s[i], mulc(om, t[i]));
-                    r[i] = ri;
-                    acc_dot<T, A>(rhat[i], ri, nr2[0], nr2[1]);
-                    nr2[2] += norm2<T, A>(ri);
+                for (int32_t i0 = threadIdx.x; i0 < n; i0 += MU2 * BT) {
+                    T xa[MU2], pa[MU2], sha[MU2], sa[MU2], ta[MU2], ha[MU2];
+#pragma unroll
+                    for (int u = 0; u < MU2; ++u) {
+                        const int32_t i = i0 + u * BT;
+                        if (i < n) {
+                            xa[u] = xd[i];
+                            pa[u] = ph[i];
+                            sha[u] = c.buf[i];
+                            sa[u] = s[i];
+                            ta[u] = t[i];
+                            ha[u] = rhat[i];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < MU2; ++u) {
+                        const int32_t i = i0 + u * BT;
+                        if (i < n) {
+                            xd[i] = addc(xa[u], addc(mulc(al, pa[u]), mulc(om, sha[u])));
+                            const T ri = subc(sa[u], mulc(om, ta[u]));
+                            r[i] = ri;
+                            acc_dot<T, A>(ha[u], ri, nr2[0], nr2[1]);
+                            nr2[2] += norm2<T, A>(ri);
+                        }
+                    }
                 }
             }
             double nrs2[3];
@@ -1018,10 +1120,14 @@ __global__ void __launch_bounds__(BT, 1) batched_solver(BatchSys* sys, int nsys,
     // The system's descriptor is copied to shared memory: kept in global
     // memory, its pointer fields would be re-read from L2 after every store.
     __shared__ __align__(16) BatchSys S;
-    __shared__ __align__(8) uint64_t ring_bars[RING];
+    __shared__ __align__(8) uint64_t ring_bars[RING_MAX];
+    __shared__ __align__(8) uint64_t ring_empty[RING_MAX];
     __shared__ int ring_abort;
     if (threadIdx.x == 0) {
-        for (int r = 0; r < RING; ++r) mbar_init(ring_bars + r, 1);
+        for (int r = 0; r < RING_MAX; ++r) {
+            mbar_init(ring_bars + r, 1);
+            mbar_init(ring_empty + r, 1);
+        }
         ring_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -1070,8 +1176,13 @@ __global__ void __launch_bounds__(BT, 1) batched_solver(BatchSys* sys, int nsys,
         {
             const size_t vb = ((size_t)S.n * (MIXED ? sizeof(float2) : sizeof(double2)) + 15) & ~size_t(15);
             sm.buf = smem;
-            int32_t* lv = reinterpret_cast<int32_t*>(smem + vb);
             size_t off = vb;
+            sm.pbuf = nullptr;
+            if (MIXED && P.pbuf_smem) {
+                sm.pbuf = smem + off;
+                off += vb;
+            }
+            int32_t* lv = reinterpret_cast<int32_t*>(smem + off);
             if (P.lvl_smem) {
                 const int nlo = S.lo.nlev + 1, nup = S.up.nlev + 1;
                 for (int t = threadIdx.x; t < nlo; t += BT) lv[t] = S.lo.lvl[t];
@@ -1085,10 +1196,12 @@ __global__ void __launch_bounds__(BT, 1) batched_solver(BatchSys* sys, int nsys,
             }
             sm.ring.base = smem + off;
             sm.ring.bars = ring_bars;
+            sm.ring.empty = ring_empty;
             sm.ring.abort = &ring_abort;
             sm.ring.err = err;
             sm.ring.slot_bytes = P.ring_slot_bytes;
             sm.ring.umax = P.ring_umax;
+            sm.ring.nslots = P.ring_slots;
             sm.ring.seq = ring_seq;
         }
         __syncthreads();
@@ -1123,39 +1236,60 @@ size_t slot_bytes_of(int E, int R, int umax) {
     return (size_t)L.dinv + (size_t)umax * dinv_stride<T>(R);
 }
 
-// Dynamic shared memory of a launch for a given plan (lvl_smem, umax).
+// Dynamic shared memory of a launch for a given plan: the solve vector, p^
+// (pbuf), the level boundaries (lvl_smem) and nslots ring slots of umax units.
 template <class T>
-size_t plan_bytes(const std::vector<BatchShape>& shapes, int lvl_smem, int umax, size_t* slot_out) {
+size_t plan_bytes(const std::vector<BatchShape>& shapes, int pbuf, int lvl_smem, int umax, int nslots,
+                  size_t* slot_out) {
     size_t base = 0, slot = 0;
     for (const BatchShape& b : shapes) {
-        size_t v = ((size_t)b.n * sizeof(T) + 15) & ~size_t(15);
+        const size_t vb = ((size_t)b.n * sizeof(T) + 15) & ~size_t(15);
+        size_t v = vb * (pbuf ? 2 : 1);
         if (lvl_smem) v += ((size_t)(b.nlev_lo + b.nlev_up + 2) * 4 + 15) & ~size_t(15);
         base = std::max(base, v);
         if (umax > 0)
             slot = std::max(slot, std::max(slot_bytes_of<T>(b.E_lo, b.R_lo, umax), slot_bytes_of<T>(b.E_up, b.R_up, umax)));
     }
     *slot_out = slot;
-    return base + (size_t)RING * slot;
+    return base + (size_t)nslots * slot;
 }
 
+// Units per staged level: the widest level of any system (at most one per warp).
+int widest_level(const std::vector<BatchShape>& shapes) {
+    int u = 1;
+    for (const BatchShape& b : shapes) u = std::max(u, b.umax);
+    return std::min(u, NW);
+}
+
+// Preference: level boundaries in shared memory; a deep ring (every level's
+// data is requested nslots - 1 levels ahead, which has to cover the memory
+// latency); p^ in shared memory (mixed precision) only next to a deep ring.
 template <class T>
 size_t choose_plan(const std::vector<BatchShape>& shapes, size_t cap, BatchParams& p) {
+    struct Try { int pbuf, min_slots; };
+    const Try tries[] = {{p.mixed ? 1 : 0, 12}, {0, 4}, {0, 2}};
     for (int lvl_smem = 1; lvl_smem >= 0; --lvl_smem)
-        for (int umax = p.ring_allowed ? NW : 0; umax >= 1; umax >>= 1) {
-            size_t slot = 0;
-            const size_t b = plan_bytes<T>(shapes, lvl_smem, umax, &slot);
-            if (b <= cap) {
-                p.lvl_smem = lvl_smem;
-                p.ring_umax = umax;
-                p.ring_slot_bytes = (int)slot;
-                return b;
-            }
-        }
+        for (int umax = p.ring_allowed ? widest_level(shapes) : 0; umax >= 1; umax = umax > 4 ? umax / 2 : umax - 1)
+            for (const Try& t : tries)
+                for (int ns = RING_MAX; ns >= t.min_slots; --ns) {
+                    size_t slot = 0;
+                    const size_t b = plan_bytes<T>(shapes, t.pbuf, lvl_smem, umax, ns, &slot);
+                    if (b <= cap) {
+                        p.lvl_smem = lvl_smem;
+                        p.pbuf_smem = t.pbuf;
+                        p.ring_umax = umax;
+                        p.ring_slots = ns;
+                        p.ring_slot_bytes = (int)slot;
+                        return b;
+                    }
+                }
     size_t slot = 0;
     p.lvl_smem = 0;
+    p.pbuf_smem = 0;
     p.ring_umax = 0;
+    p.ring_slots = 0;
     p.ring_slot_bytes = 0;
-    return plan_bytes<T>(shapes, 0, 0, &slot);
+    return plan_bytes<T>(shapes, 0, 0, 0, 0, &slot);
 }
 
 }  // namespace

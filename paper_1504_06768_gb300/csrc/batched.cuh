@@ -11,7 +11,7 @@
 
 constexpr int BATCH_THREADS = 512;
 constexpr int BATCH_MAXE = 3;       // packed entry slots per lane and unit (longer rows overflow to the CSR)
-constexpr int BATCH_RING = 4;       // shared-memory slots staging triangular-solve levels
+constexpr int BATCH_RING_MAX = 16;  // shared-memory slots staging triangular-solve levels, at most
 
 // Lane-major packed layout of one CSR operand (a strict triangle of the
 // factors, or A itself).  Rows are grouped into units of R = 32 / G rows
@@ -78,12 +78,15 @@ struct BatchParams {
     int ring_allowed;           // every staged array is 16-byte aligned (bulk copies may be used)
     // shared-memory plan of the launch (set by batch_launch)
     int ring_umax;              // units per staged level (0: no ring)
+    int ring_slots;             // slots of the ring
     int ring_slot_bytes;
     int lvl_smem;               // level boundaries copied to shared memory
+    int pbuf_smem;              // mixed precision: p^ kept in shared memory
 };
 
 struct BatchShape {             // what the shared-memory plan needs of one system
     int32_t n, nlev_lo, nlev_up, E_lo, R_lo, E_up, R_up;
+    int32_t umax;               // units in the widest level of either triangle
 };
 
 // ------------------------------------------------------- batched setup
