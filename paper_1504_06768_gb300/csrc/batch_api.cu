@@ -25,9 +25,15 @@ double now_ms() {
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
-int lanes_for(double avg) {
+// Lanes per row of a packed operand: the fewest whose BATCH_MAXE packed slots
+// hold 99 % of the rows (fewer lanes: less padding and fewer shuffle rounds;
+// the longer rows finish from the CSR).
+int lanes_for_triangle(std::vector<int32_t> lens) {
+    if (lens.empty()) return 1;
+    std::sort(lens.begin(), lens.end());
+    const int32_t p99 = lens[(size_t)(0.99 * (double)(lens.size() - 1))];
     int g = 1;
-    while (g < 32 && 2.0 * g < avg) g <<= 1;
+    while (g < 32 && g * BATCH_MAXE < p99) g <<= 1;
     return g;
 }
 
@@ -139,9 +145,20 @@ void build_pattern_host(Pattern& P, int use_rcm) {
     std::vector<int32_t> uorder, uptr;
     P.n_levels = level_sets_host(n, prp.data(), pcol.data(), true, P.lorder, P.lptr);
     P.up_levels = level_sets_host(n, prp.data(), pcol.data(), false, uorder, uptr);
-    P.lo_g = lanes_for(n ? (double)lo / n : 1.0);
-    P.up_g = lanes_for(n ? (double)up / n : 1.0);
-    P.a_g = lanes_for(n ? (double)P.col.size() / n : 1.0);
+    {
+        std::vector<int32_t> llen(n), ulen(n);
+        for (int64_t r = 0; r < n; ++r) {
+            llen[r] = P.dpos[r] - prp[r];
+            ulen[r] = prp[r + 1] - P.dpos[r] - 1;
+        }
+        P.lo_g = lanes_for_triangle(std::move(llen));
+        P.up_g = lanes_for_triangle(std::move(ulen));
+    }
+    {
+        std::vector<int32_t> alen(n);
+        for (int64_t r = 0; r < n; ++r) alen[r] = prp[r + 1] - prp[r];
+        P.a_g = lanes_for_triangle(std::move(alen));
+    }
     level_units_host(P.lorder, P.lptr, 32 / P.lo_g, P.lunits);
     level_units_host(uorder, uptr, 32 / P.up_g, P.uunits);
     P.lo_nunits = (int32_t)(P.lunits.size() / (32 / P.lo_g));

@@ -320,34 +320,41 @@ __device__ void cta_trsv_ring(const PackedOp& P, const int32_t* lvl, const int32
             }
         __syncwarp();
     } else {
+        const T* sv0 = reinterpret_cast<const T*>(rg.base);
+        int32_t beg = lvl[0];
         for (int32_t l = 0; l < nlev; ++l) {
             const uint32_t q = s0 + l;
             const int slot = q % ns;
-            const int32_t beg = lvl[l], cnt = lvl[l + 1] - beg;
-            if (warp < cnt) ring_wait(rg, slot, (q / ns) & 1u);        // warps without a unit do not read the slot
-            const unsigned char* sb = rg.base + (size_t)slot * rg.slot_bytes;
-            for (int32_t u = warp; u < cnt; u += NW - 1) {
-                UnitRegs<T> cu;
-                T dinv = zero<T>();
-                if (u < umax) {
-                    const T* sv = reinterpret_cast<const T*>(sb);
-                    const int32_t* sc = reinterpret_cast<const int32_t*>(sb + sl.col);
-                    const int4 m = reinterpret_cast<const int4*>(sb + sl.meta)[u * R + grp];
+            const int32_t end = lvl[l + 1], cnt = end - beg;
+            if (warp < cnt) {                       // warps without a unit do not read the slot
+                ring_wait(rg, slot, (q / ns) & 1u);
+                const unsigned char* sb = reinterpret_cast<const unsigned char*>(sv0) + (size_t)slot * rg.slot_bytes;
+                const T* sv = reinterpret_cast<const T*>(sb) + lane;
+                const int32_t* sc = reinterpret_cast<const int32_t*>(sb + sl.col) + lane;
+                const int4* sm4 = reinterpret_cast<const int4*>(sb + sl.meta) + grp;
+                const T* sd = reinterpret_cast<const T*>(sb + sl.dinv) + grp;
+                for (int32_t u = warp; u < cnt; u += NW - 1) {
+                    UnitRegs<T> cu;
+                    T dinv = zero<T>();
+                    if (u < umax) {
+                        const int4 m = sm4[u * R];
 #pragma unroll
-                    for (int q2 = 0; q2 < MAXE; ++q2) {
-                        cu.jj[q2] = q2 < E ? sc[(u * E + q2) * 32 + lane] : -1;
-                        cu.vv[q2] = q2 < E ? sv[(u * E + q2) * 32 + lane] : zero<T>();
+                        for (int q2 = 0; q2 < MAXE; ++q2) {
+                            cu.jj[q2] = q2 < E ? sc[(u * E + q2) * 32] : -1;
+                            cu.vv[q2] = q2 < E ? sv[(u * E + q2) * 32] : zero<T>();
+                        }
+                        cu.i = m.x;
+                        cu.ob = m.y;
+                        cu.oe = m.z;
+                        if (!LOWER) dinv = sd[u * dstride];
+                    } else {
+                        load_unit<G, T>(P, beg + u, lane, cu);
+                        if (!LOWER && cu.i >= 0) dinv = inv[cu.i];
                     }
-                    cu.i = m.x;
-                    cu.ob = m.y;
-                    cu.oe = m.z;
-                    if (!LOWER) dinv = reinterpret_cast<const T*>(sb + sl.dinv)[u * dstride + grp];
-                } else {
-                    load_unit<G, T>(P, beg + u, lane, cu);
-                    if (!LOWER && cu.i >= 0) dinv = inv[cu.i];
+                    solve_row<LOWER, G, T>(cu, dinv, ocol, oval, buf, sub);
                 }
-                solve_row<LOWER, G, T>(cu, dinv, ocol, oval, buf, sub);
             }
+            beg = end;
             named_barrier(1, CONSUMERS);
             if (threadIdx.x == 0) mbar_arrive(rg.empty + slot);      // the slot may be refilled
         }
@@ -1112,7 +1119,7 @@ __device__ void finalise(const BatchSys& S, double* red) {
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(BT, 1) batched_solver(BatchSys* sys, int nsys, BatchParams P, int* queue,
+__global__ void __launch_bounds__(BT, BATCH_BLOCKS_PER_SM) batched_solver(BatchSys* sys, int nsys, BatchParams P, int* queue,
                                                          int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[NW * 3 + 3];
@@ -1296,15 +1303,18 @@ size_t choose_plan(const std::vector<BatchShape>& shapes, size_t cap, BatchParam
 
 ss_status batch_launch(ss_ctx ctx, BatchSys* dsys, int nsys, BatchParams p, const std::vector<BatchShape>& shapes,
                        int* queue, int* err) {
-    int optin = 0;
+    int optin = 0, per_sm = 0;
     SS_CUDA(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    SS_CUDA(ctx, cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+    // every resident block needs its share of the SM (and 1 KiB the system reserves per block)
+    optin = std::min(optin, per_sm / BATCH_BLOCKS_PER_SM - 1024);
     cudaFuncAttributes fa;
     if (p.mixed) SS_CUDA(ctx, cudaFuncGetAttributes(&fa, batched_solver<true>));
     else SS_CUDA(ctx, cudaFuncGetAttributes(&fa, batched_solver<false>));
     const size_t cap = (size_t)optin > fa.sharedSizeBytes + 256 ? (size_t)optin - fa.sharedSizeBytes - 256 : 0;
     const size_t smem = p.mixed ? choose_plan<float2>(shapes, cap, p) : choose_plan<double2>(shapes, cap, p);
     if (smem > cap) return set_error(ctx, SS_ERR_UNSUPPORTED, "system too large for the per-system solver's shared memory");
-    const int grid = std::max(1, std::min(nsys, ctx->num_sms > 0 ? ctx->num_sms : 1));
+    const int grid = std::max(1, std::min(nsys, BATCH_BLOCKS_PER_SM * (ctx->num_sms > 0 ? ctx->num_sms : 1)));
     if (p.mixed) {
         SS_CUDA(ctx, cudaFuncSetAttribute(batched_solver<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         ProfScope ps(ctx, PROF_BATCHED);

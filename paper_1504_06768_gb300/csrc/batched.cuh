@@ -9,7 +9,8 @@
 
 #include "common.cuh"
 
-constexpr int BATCH_THREADS = 512;
+constexpr int BATCH_THREADS = 512;     // threads of one solver block
+constexpr int BATCH_BLOCKS_PER_SM = 1; // solver blocks resident per SM (each solves its own system)
 constexpr int BATCH_MAXE = 3;       // packed entry slots per lane and unit (longer rows overflow to the CSR)
 constexpr int BATCH_RING_MAX = 16;  // shared-memory slots staging triangular-solve levels, at most
 
