@@ -317,9 +317,11 @@ def run_gpu(args):
         for f in ("batched.cu", "batched.cuh"):
             h.update(open(os.path.join(ROOT, "paper_1504_06768_gb300", "csrc", f), "rb").read())
         if (tr.get("kernel") == dom and tr.get("workload") == "jc40" and tr.get("precision") == args.precision
-                and tr.get("batch") == BATCH and tr.get("source_sha256") == h.hexdigest()):
-            roofline["traffic"] = tr.get("bytes_per_launch")
-            roofline["traffic_source"] = "profiles/" + tr.get("summary", "traffic.json")
+                and tr.get("source_sha256") == h.hexdigest()):
+            # captured on a smaller batch; DRAM bytes scale with the system-iterations a launch runs
+            roofline["traffic"] = int(tr["bytes_per_system_iteration"] * total_iters / max(args.steps, 1))
+            roofline["traffic_source"] = ("profiles/" + tr.get("summary", "traffic.json") +
+                                          f" (batch {tr.get('captured_batch')}, scaled by system-iterations)")
 
     launches_per_step = sum(prof[k][0] for k in prof) / args.steps
     resid = max(i["resid_Lrho"] for i in step_infos)
