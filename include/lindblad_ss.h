@@ -54,7 +54,8 @@ typedef enum {
 } ss_status;
 
 typedef enum {
-    SS_METHOD_DIRECT = 0,          /* direct LU of Eq. (linear): not built (returns UNSUPPORTED) */
+    SS_METHOD_DIRECT = 0,          /* LU with partial pivoting of the RCM-ordered Eq. (linear) as a band (section
+                                      "Direct factorization"); SS_ERR_UNSUPPORTED when the band is too wide */
     SS_METHOD_ITER_GMRES = 1,      /* "iterative-lgmres": restarted GMRES(m) on Eq. (linear) */
     SS_METHOD_ITER_BICGSTAB = 2,   /* "iterative-bicgstab": BiCGSTAB on Eq. (linear)         */
     SS_METHOD_INVERSE_POWER = 3    /* doubly-iterative inverse power on L - sigma I          */

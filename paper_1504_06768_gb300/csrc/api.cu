@@ -10,6 +10,7 @@
 #include "krylov.cuh"
 #include "solver_util.cuh"
 #include "spmv.cuh"
+#include "direct.cuh"
 
 namespace {
 
@@ -432,6 +433,69 @@ extern "C" ss_status krylov_solve(ss_ctx ctx, ss_mat A, ss_prec M, int krylov, c
 }
 
 // Steady state of one system (all §-references are to the paper).
+namespace {
+
+// method=direct: x = L~^{-1} (w e_0) by the banded LU (direct.cu), acceptance
+// test ||L rho||_2 <= tol on the trace-normalised rho, finalisation.  Takes
+// ownership of Ap.
+ss_status steady_state_direct(ss_ctx ctx, ss_mat Ap, const std::vector<int32_t>& perm, int64_t d, double w_used,
+                              const ss_options& opt, double t0, ss_info inf, double* rho_out, int rho_on_device,
+                              ss_info* info) {
+    const int64_t n = Ap->m.n_rows;
+    std::vector<int32_t> iperm(n), tidx(d);
+    for (int64_t r = 0; r < n; ++r) iperm[perm[r]] = (int32_t)r;
+    for (int64_t i = 0; i < d; ++i) tidx[i] = iperm[i * (d + 1)];
+    const int64_t r0 = iperm[0];
+    int32_t *perm_d = nullptr, *tidx_d = nullptr;
+    double2 *b = nullptr, *x = nullptr, *y = nullptr, *rho = nullptr, *trace_d = nullptr;
+    double* scr = nullptr;
+    ss_status st = SS_OK;
+    auto cleanup = [&]() {
+        dev_free(ctx, perm_d); dev_free(ctx, tidx_d); dev_free(ctx, b); dev_free(ctx, x); dev_free(ctx, y);
+        dev_free(ctx, rho); dev_free(ctx, trace_d); dev_free(ctx, scr);
+        ss_mat_free(Ap);
+    };
+#define DSTEP(call) do { st = (call); if (st != SS_OK) { cleanup(); return st; } } while (0)
+    DSTEP(dev_alloc_n(ctx, &perm_d, (size_t)n));
+    DSTEP(dev_alloc_n(ctx, &tidx_d, (size_t)d));
+    DSTEP(dev_alloc_n(ctx, &b, (size_t)n));
+    DSTEP(dev_alloc_n(ctx, &x, (size_t)n));
+    DSTEP(dev_alloc_n(ctx, &y, (size_t)n));
+    DSTEP(dev_alloc_n(ctx, &rho, (size_t)n));
+    DSTEP(dev_alloc_n(ctx, &trace_d, 1));
+    DSTEP(dev_alloc_n(ctx, &scr, (size_t)su_scratch_doubles()));
+    SS_CUDA(ctx, cudaMemcpyAsync(perm_d, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+    SS_CUDA(ctx, cudaMemcpyAsync(tidx_d, tidx.data(), sizeof(int32_t) * d, cudaMemcpyHostToDevice, ctx->stream));
+    DSTEP(su_zero(ctx, n, b));
+    const double2 wb = make_double2(w_used, 0.0);
+    SS_CUDA(ctx, cudaMemcpyAsync(b + r0, &wb, sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+    const double t1 = now_ms();
+    BandInfo bi;
+    DSTEP(band_lu_solve(ctx, Ap->m, b, x, &bi));
+    double lr = INFINITY;
+    DSTEP(su_lrho(ctx, Ap->m, x, 0, w_used, r0, d, tidx_d, y, scr, trace_d, &lr, nullptr));
+    DSTEP(su_trace(ctx, d, tidx_d, x, trace_d));
+    DSTEP(su_finalise(ctx, n, perm_d, x, trace_d, rho));
+    SS_CUDA(ctx, cudaMemcpyAsync(rho_out, rho, sizeof(double2) * n,
+                                 rho_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int status = lr <= opt.tol ? SS_OK : SS_NOT_CONVERGED;
+    inf.status = status;
+    inf.iters = 0;
+    inf.outer_iters = 1;
+    inf.resid_Lrho = lr;
+    inf.nnz_factors = n * (2 * bi.kl + bi.ku + 1);      // band entries of L and U
+    inf.ms_setup = t1 - t0;
+    inf.ms_solve = now_ms() - t1;
+    if (info) *info = inf;
+    cleanup();
+#undef DSTEP
+    if (status != SS_OK) ctx->last_error = "direct solve: ||L rho|| above tol (rounding of an ill-conditioned system)";
+    return (ss_status)status;
+}
+
+}  // namespace
+
 extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, const ss_csr_view* c_ops,
                                   const ss_options* opt_in, double* rho_out, int rho_on_device, ss_info* info) {
     SS_TRY(check_ctx(ctx));
@@ -439,11 +503,10 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
     ss_options_default(&opt);
     if (opt_in) opt = *opt_in;
     if (!rho_out || !H) return set_error(ctx, SS_ERR_INVALID, "null argument");
-    if (opt.method == SS_METHOD_DIRECT)
-        return set_error(ctx, SS_ERR_UNSUPPORTED, "method=direct is not built; use an iterative method");
-    if (opt.method < SS_METHOD_ITER_GMRES || opt.method > SS_METHOD_INVERSE_POWER)
+    if (opt.method < SS_METHOD_DIRECT || opt.method > SS_METHOD_INVERSE_POWER)
         return set_error(ctx, SS_ERR_INVALID, "unknown method");
     const bool mixed = opt.precision == SS_PREC_MIXED;
+    const bool direct = opt.method == SS_METHOD_DIRECT;
     if (mixed && opt.method != SS_METHOD_ITER_BICGSTAB)
         return set_error(ctx, SS_ERR_UNSUPPORTED, "mixed precision is built for iterative-bicgstab only");
     if (!(opt.tol > 0.0) || opt.maxiter < 1) return set_error(ctx, SS_ERR_INVALID, "tol must be > 0, maxiter >= 1");
@@ -474,6 +537,7 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
     inf.nnz = Ap->m.nnz;
     inf.w_used = w_used;
     bandwidth_profile_impl(ctx, Ap->m, &inf.bandwidth, &inf.profile);
+    if (direct) return steady_state_direct(ctx, Ap, perm, d, w_used, opt, t0, inf, rho_out, rho_on_device, info);
     st = build_prec(ctx, Ap->m, opt.precond, opt.drop_tol, opt.fill_factor, mixed, &M);
     if (st == SS_OK && mixed) st = ensure_f32(ctx, Ap);
     if (st != SS_OK) { ss_mat_free(Ap); return st; }

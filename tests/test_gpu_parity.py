@@ -11,7 +11,7 @@ from oracle.metrics import hermiticity_error, min_eigenvalue, trace_distance
 from oracle.ordering import bandwidth_profile as o_bwp
 from oracle.ordering import permute_symmetric, rcm_order
 from oracle.steady import steady_state_dense
-from workloads import (driven_cavity, jaynes_cummings_rwa, kerr_chain, kerr_oscillator, optomechanics,
+from workloads import (driven_cavity, jaynes_cummings_rwa, kerr_chain, kerr_oscillator, kerr_sweep, optomechanics,
                        paper_jc_nonrwa, paper_optomechanics, paper_spin_chain, random_system, thermal_cavity,
                        two_level_atom)
 
@@ -309,9 +309,17 @@ def test_invalid_inputs_reported(ss):
     with pytest.raises(ss.SolverError) as e:
         ss.steady_state(s.H, [sp.identity(3, dtype=complex, format="csr")])
     assert e.value.status == 1
-    with pytest.raises(ss.SolverError) as e:
-        ss.steady_state(s.H, s.c_ops, method="direct")
-    assert e.value.status == 8
+    import ctypes as C
+    from paper_1504_06768_gb300 import _binding as B
+    opt = ss._options("direct", 1e-10, "ilu0", "fp64", 1000, 30, 1e-4, 10.0, 0.0, 1e-15, True, 0)
+    opt.method = 9                                                    # no such method
+    hv = ss._CsrHost(s.H)
+    cvs = [ss._CsrHost(c) for c in s.c_ops]
+    arr = (B.CsrView * len(cvs))(*[c.view for c in cvs])
+    rho = np.empty(s.d * s.d, dtype=np.complex128)
+    ctx = ss.get_context()
+    assert B.load().steady_state(ctx.handle, C.byref(hv.view), len(cvs), arr, C.byref(opt), rho.ctypes.data, 0,
+                                 None) == 1
 
 
 # ------------------------------------------------------------ steady state
@@ -411,3 +419,38 @@ def test_mixed_single_system_small(ss, name):
     rho, info = ss.steady_state(s.H, s.c_ops, precision="mixed", tol=1e-11)
     assert info["status"] == 0 and info["resid_Lrho"] <= 1e-11 and info["outer_iters"] >= 2
     assert trace_distance(rho, steady_state_dense(s.H, s.c_ops)) <= 1e-8
+
+
+# ------------------------------------------------------------ direct method
+
+@pytest.mark.parametrize("maker", [lambda: driven_cavity(n_th=0.0), lambda: driven_cavity(n_th=0.2),
+                                   lambda: thermal_cavity(n_th=0.2), lambda: two_level_atom(),
+                                   lambda: jaynes_cummings_rwa(seed=2, N=12), lambda: kerr_sweep(1, seed=4)[0]],
+                         ids=["coherent", "thermal_driven", "thermal", "two_level", "jc12", "kerr"])
+def test_direct_banded_lu_matches_oracle(ss, maker):
+    """method=direct: banded LU with partial pivoting of the RCM-ordered L~ on
+    the device, against the dense FP64 LU of the oracle."""
+    s = maker()
+    rho, info = ss.steady_state(s.H, s.c_ops, method="direct", tol=1e-10)
+    assert info["status"] == 0 and info["iters"] == 0 and info["resid_Lrho"] <= 1e-10
+    assert trace_distance(rho, steady_state_dense(s.H, s.c_ops)) <= 1e-10
+    assert abs(np.trace(rho) - 1) < 1e-12
+
+
+def test_direct_jc40_full_size(ss):
+    s = jaynes_cummings_rwa(seed=0)
+    rho, info = ss.steady_state(s.H, s.c_ops, method="direct", tol=1e-10)
+    assert info["status"] == 0 and info["n"] == 6400
+    assert trace_distance(rho, steady_state_dense(s.H, s.c_ops)) <= 1e-10
+
+
+def test_direct_closed_form_coherent_state(ss):
+    """The driven damped cavity's coherent steady state, alpha = -iE/(i Delta + kappa/2)."""
+    s = driven_cavity(N=30, n_th=0.0)
+    rho, info = ss.steady_state(s.H, s.c_ops, method="direct", tol=1e-10)
+    delta, E, kappa = 0.5, 0.3, 1.0
+    alpha = -1j * E / (1j * delta + kappa / 2)
+    from math import factorial
+    n = np.arange(30)
+    psi = np.exp(-abs(alpha) ** 2 / 2) * alpha ** n / np.sqrt(np.array([float(factorial(int(k))) for k in n]))
+    assert trace_distance(rho, np.outer(psi, psi.conj())) <= 1e-12
