@@ -85,6 +85,7 @@ struct TriLevels {                    // level-scheduled triangular factor
     int32_t n_levels = 0;
     int32_t* order = nullptr;         // rows sorted by level (device, n)
     int32_t* units = nullptr;         // level-aligned units of 32/g rows, -1 padded (device)
+    int4* meta = nullptr;             // per unit row: {row, first entry, end of the triangle's part} (device)
     int64_t n_units = 0;
     int g = 32;                       // lanes per row in the solve
 };

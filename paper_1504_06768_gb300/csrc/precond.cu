@@ -84,15 +84,21 @@ template <> __device__ __forceinline__ float2 pending<float2>() {
 //          `other[i]` (the upper solve's output) PENDING.
 //   UPPER: x_i = (b_i - sum_{j>i} u_ij x_j) / u_ii; afterwards re-marks b_i
 //          (the lower solve's output) PENDING for the next application.
+// A row's range comes from a precomputed record {row, first, end, -} of its
+// unit, and in FP32 each lane issues the column and value loads of its next
+// SYNCFREE_K entries, then their x loads, before it waits on any of them, so a
+// row costs three dependent memory round trips when its inputs are ready.
+constexpr int SYNCFREE_K = 4;
+
 template <bool LOWER, int G, class T>
-__global__ void __launch_bounds__(256) sptrsv_syncfree(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                       const T* __restrict__ val, const int32_t* __restrict__ dpos,
-                                                       const T* __restrict__ inv_diag, const int32_t* __restrict__ units,
+__global__ void __launch_bounds__(256) sptrsv_syncfree(const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                       const T* __restrict__ inv_diag, const int4* __restrict__ meta,
                                                        int64_t n_units, T* b, T* x, T* other,
                                                        unsigned long long* __restrict__ ticket, int* __restrict__ err,
                                                        const int* __restrict__ halt) {
     using C = Cplx<T>;
     constexpr int R = 32 / G;
+    constexpr int K = sizeof(T) == 16 ? 1 : SYNCFREE_K;   // FP64: registers of more in-flight entries cost more
     if (halt && *halt) return;      // uniform over the launch: no ticket is taken
     __shared__ unsigned long long s_ticket;
     if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1ull);
@@ -103,33 +109,42 @@ __global__ void __launch_bounds__(256) sptrsv_syncfree(const int32_t* __restrict
     if (u >= n_units) return;
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane % G;
-    const int32_t i = units[u * R + grp];          // -1 pads a unit at the end of a level
-    int32_t s = 0, e = 0;
-    if (i >= 0) {
-        if (LOWER) { s = rp[i]; e = dpos[i]; }
-        else { s = dpos[i] + 1; e = rp[i + 1]; }
-    }
+    const int4 m = meta[u * R + grp];              // row -1 pads a unit at the end of a level
+    const int32_t i = m.x, s = m.y, e = m.z;
+    T dinv = C::zero();
+    if (!LOWER && i >= 0 && sub == 0) dinv = inv_diag[i];
     T acc = C::zero();
     bool timed_out = false;
-    for (int32_t k = s + sub; k < e; k += G) {
-        const T v = val[k];
-        const T* xp = &x[col[k]];
-        T xj = __ldcv(xp);
-        if (!ready(xj)) {
-            const unsigned long long t0 = globaltimer_ns();
-            int spins = 0;
-            while (true) {
-                if (++spins > 64) __nanosleep(64);
-                xj = __ldcv(xp);
-                if (ready(xj)) break;
-                if ((spins & 63) == 0 && (*(volatile int*)err != 0 || globaltimer_ns() - t0 > WAIT_NS)) {
-                    timed_out = true;
-                    xj = C::zero();
-                    break;
+    for (int32_t base = s + sub; base < e; base += K * G) {
+        int32_t c[K];
+        T v[K], xj[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const int32_t k = base + q * G;
+            c[q] = k < e ? col[k] : -1;
+            v[q] = k < e ? val[k] : C::zero();
+        }
+#pragma unroll
+        for (int q = 0; q < K; ++q) xj[q] = c[q] >= 0 ? __ldcv(&x[c[q]]) : C::zero();
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            if (c[q] >= 0 && !ready(xj[q])) {
+                const T* xp = &x[c[q]];
+                const unsigned long long t0 = globaltimer_ns();
+                int spins = 0;
+                while (true) {
+                    if (++spins > 64) __nanosleep(64);
+                    xj[q] = __ldcv(xp);
+                    if (ready(xj[q])) break;
+                    if ((spins & 63) == 0 && (*(volatile int*)err != 0 || globaltimer_ns() - t0 > WAIT_NS)) {
+                        timed_out = true;
+                        xj[q] = C::zero();
+                        break;
+                    }
                 }
             }
+            acc = C::fma_(v[q], xj[q], acc);
         }
-        acc = C::fma_(v, xj, acc);
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
@@ -140,7 +155,7 @@ __global__ void __launch_bounds__(256) sptrsv_syncfree(const int32_t* __restrict
     if (__any_sync(FULL, timed_out) && lane == 0) atomicExch(err, 1);
     if (i >= 0 && sub == 0) {
         T xi = C::sub(b[i], acc);
-        if (!LOWER) xi = C::mul(xi, inv_diag[i]);
+        if (!LOWER) xi = C::mul(xi, dinv);
         __stcg(&x[i], xi);
         if (LOWER) __stcg(&other[i], pending<T>());
         else __stcg(&b[i], pending<T>());
@@ -222,7 +237,8 @@ __global__ void check_missing_diag(const int32_t* __restrict__ dpos, int64_t n, 
 }
 
 ss_status upload_levels(ss_ctx ctx, const std::vector<int32_t>& order, const std::vector<int32_t>& lptr,
-                        double avg_row, TriLevels& L, int32_t nlev) {
+                        double avg_row, TriLevels& L, int32_t nlev, bool lower, const std::vector<int32_t>& hrp,
+                        const std::vector<int32_t>& hdpos) {
     L.n_levels = nlev;
     int g = 2;
     while (g < 32 && g < avg_row) g <<= 1;
@@ -230,6 +246,18 @@ ss_status upload_levels(ss_ctx ctx, const std::vector<int32_t>& order, const std
     std::vector<int32_t> units;
     level_units_host(order, lptr, 32 / g, units);
     L.n_units = (int64_t)units.size() / (32 / g);
+    // per unit row: {row, first entry, end} of the triangle's part of the row
+    std::vector<int4> meta(units.size());
+    for (size_t k = 0; k < units.size(); ++k) {
+        const int32_t i = units[k];
+        if (i < 0) meta[k] = make_int4(-1, 0, 0, 0);
+        else if (hdpos[i] < 0) meta[k] = make_int4(i, 0, 0, 0);     // no diagonal: reported as a zero pivot
+        else if (lower) meta[k] = make_int4(i, hrp[i], hdpos[i], 0);
+        else meta[k] = make_int4(i, hdpos[i] + 1, hrp[i + 1], 0);
+    }
+    SS_TRY(dev_alloc_n(ctx, &L.meta, meta.size()));
+    SS_CUDA(ctx, cudaMemcpyAsync(L.meta, meta.data(), sizeof(int4) * meta.size(), cudaMemcpyHostToDevice,
+                                 ctx->stream));
     SS_TRY(dev_alloc_n(ctx, &L.order, order.size()));
     SS_TRY(dev_alloc_n(ctx, &L.units, units.size()));
     SS_CUDA(ctx, cudaMemcpyAsync(L.order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice,
@@ -253,8 +281,12 @@ static ss_status analyse(ss_ctx ctx, ss_prec M, const std::vector<int32_t>& hrp,
     for (int64_t i = 0; i < n; ++i)
         for (int32_t t = hrp[i]; t < hrp[i + 1] && hcol[t] < i; ++t) ++nnz_lower;
     const int64_t nnz_upper = (int64_t)hcol.size() - nnz_lower - n;
-    SS_TRY(upload_levels(ctx, lower_order, lower_ptr, n ? (double)nnz_lower / n : 1.0, M->lower, nl));
-    SS_TRY(upload_levels(ctx, upper_order, upper_ptr, n ? (double)nnz_upper / n : 1.0, M->upper, nu));
+    std::vector<int32_t> hdpos(n, -1);
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t t = hrp[i]; t < hrp[i + 1]; ++t)
+            if (hcol[t] == i) { hdpos[i] = t; break; }
+    SS_TRY(upload_levels(ctx, lower_order, lower_ptr, n ? (double)nnz_lower / n : 1.0, M->lower, nl, true, hrp, hdpos));
+    SS_TRY(upload_levels(ctx, upper_order, upper_ptr, n ? (double)nnz_upper / n : 1.0, M->upper, nu, false, hrp, hdpos));
     SS_TRY(dev_alloc_n(ctx, &M->tickets, 2));
     SS_TRY(dev_alloc_n(ctx, &M->err, 1));
     SS_TRY(dev_alloc_n(ctx, &M->tmp, (size_t)n));
@@ -343,9 +375,9 @@ static void launch_trsv(ss_ctx ctx, ss_prec M, const TriLevels& L, const T* vals
     const unsigned g = (unsigned)((L.n_units * 32 + threads - 1) / threads);
 #define SS_TRSV_CASE(GG)                                                                                    \
     case GG:                                                                                                \
-        sptrsv_syncfree<LOWER, GG, T><<<(ss_count_launch(), g), threads, 0, ctx->stream>>>(M->f.row_ptr, M->f.col, vals,        \
-                                                                       M->diag_pos, inv, L.units, L.n_units, \
-                                                                       b, x, other, ticket, M->err, halt);   \
+        sptrsv_syncfree<LOWER, GG, T><<<(ss_count_launch(), g), threads, 0, ctx->stream>>>(M->f.col, vals, inv, L.meta,  \
+                                                                       L.n_units, b, x, other, ticket,       \
+                                                                       M->err, halt);                        \
         break;
     switch (L.g) {
         SS_TRSV_CASE(2)
@@ -405,6 +437,8 @@ void prec_destroy(ss_ctx ctx, ss_prec M) {
     dev_free(ctx, M->upper.order);
     dev_free(ctx, M->lower.units);
     dev_free(ctx, M->upper.units);
+    dev_free(ctx, M->lower.meta);
+    dev_free(ctx, M->upper.meta);
     dev_free(ctx, M->flags);
     dev_free(ctx, M->tickets);
     dev_free(ctx, M->err);
