@@ -56,9 +56,16 @@ typedef enum {
 typedef enum {
     SS_METHOD_DIRECT = 0,          /* LU with partial pivoting of the RCM-ordered Eq. (linear) as a band (section
                                       "Direct factorization"); SS_ERR_UNSUPPORTED when the band is too wide */
-    SS_METHOD_ITER_GMRES = 1,      /* "iterative-lgmres": restarted GMRES(m) on Eq. (linear) */
+    SS_METHOD_ITER_GMRES = 1,      /* "iterative-lgmres": restarted GMRES(m) on Eq. (linear), augmented
+                                      with the corrections of the lgmres_k previous cycles (LGMRES,
+                                      Baker, Jessup and Manteuffel 2005) when lgmres_k > 0        */
     SS_METHOD_ITER_BICGSTAB = 2,   /* "iterative-bicgstab": BiCGSTAB on Eq. (linear)         */
-    SS_METHOD_INVERSE_POWER = 3    /* doubly-iterative inverse power on L - sigma I          */
+    SS_METHOD_INVERSE_POWER = 3,   /* doubly-iterative inverse power on L - sigma I          */
+    SS_METHOD_AUTO = 4             /* the paper's choice (sections "Results" and "Conclusion"): the RCM
+                                      bandwidths of L~ (Eq. linear) and of L - sigma I (Eq. inverse)
+                                      are compared; (L)GMRES on L~ when B(L~) <= 1.5 B(L - sigma I),
+                                      else the doubly-iterative inverse power with (L)GMRES inner
+                                      solves.  FP64 only; info.method reports the choice          */
 } ss_method;
 
 typedef enum { SS_PRECOND_ILU0 = 0, SS_PRECOND_ILUT = 1 } ss_precond_kind;
@@ -98,6 +105,8 @@ typedef struct {
     int use_rcm;           /* reverse Cuthill-McKee ordering of L~ + L~^T; 1                 */
     uint64_t seed;         /* inverse-power start vector (SplitMix64 counters); 0             */
     double inner_rtol;     /* SS_PREC_MIXED: relative tolerance of each FP32 inner solve; 1e-5 */
+    int lgmres_k;          /* GMRES: corrections of earlier cycles added to each cycle (LGMRES);
+                              0 = plain restarted GMRES; restart + lgmres_k <= 64                 */
 } ss_options;
 
 /* Per-solve diagnostics. */
@@ -113,6 +122,8 @@ typedef struct {
     int64_t nnz_factors;   /* stored entries of the incomplete factors                 */
     int32_t levels_lower, levels_upper;  /* triangular-solve level counts               */
     double ms_setup, ms_solve;           /* wall time of setup and of the iteration      */
+    int method;            /* ss_method that ran (the choice of SS_METHOD_AUTO)        */
+    int64_t bw_modified, bw_shifted;     /* SS_METHOD_AUTO: RCM bandwidths compared; else 0 */
 } ss_info;
 
 /* ---------------------------------------------------------------- context */
@@ -227,6 +238,18 @@ void ss_prec_free(ss_prec M);
  * iteration count, *resid_out (may be NULL) the final residual norm. */
 ss_status krylov_solve(ss_ctx ctx, ss_mat A, ss_prec M, int krylov, const double* b, double* x,
                        double tol, int maxiter, int restart, int* iters_out, double* resid_out);
+
+/* krylov_solve with SS_KRYLOV_GMRES augmented as LGMRES(restart, augment)
+ * (Baker, Jessup and Manteuffel 2005): each restart cycle minimises
+ * ||b - A x||_2 over M^{-1} applied to the Krylov space of the cycle's
+ * residual plus the normalised corrections of the `augment` previous cycles
+ * (each costs one product with A and no preconditioner application; both
+ * kinds of step count as iterations).  augment = 0 is GMRES(restart).
+ * Arguments and statuses as for krylov_solve.
+ * Errors: SS_ERR_INVALID unless restart >= 1, augment >= 0 and
+ * restart + augment <= 64. */
+ss_status lgmres_solve(ss_ctx ctx, ss_mat A, ss_prec M, const double* b, double* x, double tol, int maxiter,
+                       int restart, int augment, int* iters_out, double* resid_out);
 
 /* Largest system krylov_solve_noalloc accepts (complex unknowns). */
 #define SS_NOALLOC_MAX_N 65536

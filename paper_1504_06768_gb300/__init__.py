@@ -306,21 +306,26 @@ def precond_apply_f32(M: Preconditioner, r):
 
 
 def krylov_solve(A: Matrix, M: Preconditioner, b, x0=None, method: str = "bicgstab", tol: float = 1e-12,
-                 maxiter: int = 1000, restart: int = 30, raise_on_failure: bool = False):
-    """Right-preconditioned BiCGSTAB / GMRES(m) on A x = b; returns (x, status, iters, resid)."""
+                 maxiter: int = 1000, restart: int = 30, raise_on_failure: bool = False, augment: int = 0):
+    """Right-preconditioned BiCGSTAB / GMRES(m) on A x = b; method "lgmres"
+    runs LGMRES(restart, augment).  Returns (x, status, iters, resid)."""
     import torch
     n = A.shape[0]
     x = torch.zeros_like(b) if x0 is None else x0.clone()
     it, res = C.c_int(), C.c_double()
-    st = B.load().krylov_solve(A.ctx.handle, A.handle, M.handle, B.KRYLOV[method], _dev_ptr(b, "c128", n),
-                               _dev_ptr(x, "c128", n), tol, maxiter, restart, C.byref(it), C.byref(res))
+    if method == "lgmres":
+        st = B.load().lgmres_solve(A.ctx.handle, A.handle, M.handle, _dev_ptr(b, "c128", n), _dev_ptr(x, "c128", n),
+                                   tol, maxiter, restart, augment, C.byref(it), C.byref(res))
+    else:
+        st = B.load().krylov_solve(A.ctx.handle, A.handle, M.handle, B.KRYLOV[method], _dev_ptr(b, "c128", n),
+                                   _dev_ptr(x, "c128", n), tol, maxiter, restart, C.byref(it), C.byref(res))
     if st not in (B.SS_OK, B.SS_NOT_CONVERGED, B.SS_BREAKDOWN) or (raise_on_failure and st != 0):
         A.ctx.check(st, "krylov_solve")
     return x, st, it.value, res.value
 
 
 def _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed,
-             inner_rtol=1e-5):
+             inner_rtol=1e-5, lgmres_k=0):
     opt = B.Options()
     B.load().ss_options_default(C.byref(opt))
     opt.method = B.METHODS[method]
@@ -330,6 +335,7 @@ def _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_f
     opt.drop_tol, opt.fill_factor, opt.w, opt.sigma = drop_tol, fill_factor, w, sigma
     opt.use_rcm, opt.seed = int(bool(use_rcm)), seed
     opt.inner_rtol = inner_rtol
+    opt.lgmres_k = lgmres_k
     return opt
 
 
@@ -337,7 +343,7 @@ def steady_state_batched(systems: Sequence, method: str = "iterative-bicgstab", 
                          precond: str = "ilu0", precision: str = "fp64", maxiter: int = 1000, restart: int = 30,
                          drop_tol: float = 1e-4, fill_factor: float = 10.0, w: float = 0.0, sigma: float = 1e-15,
                          use_rcm: bool = True, seed: int = 0, ctx: Optional[Context] = None,
-                         raise_on_failure: bool = True, inner_rtol: float = 1e-5):
+                         raise_on_failure: bool = True, inner_rtol: float = 1e-5, lgmres_k: int = 0):
     """Steady states of many systems, each given as (H, c_ops); returns a list
     of rho (numpy, d x d) and a list of info dicts."""
     ctx = ctx or get_context()
@@ -351,7 +357,7 @@ def steady_state_batched(systems: Sequence, method: str = "iterative-bicgstab", 
     outs = (C.c_void_p * max(ns, 1))(*[r.ctypes.data for r in rhos])
     infos = (B.Info * max(ns, 1))()
     opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed,
-                   inner_rtol)
+                   inner_rtol, lgmres_k)
     st = B.load().steady_state_batched(ctx.handle, ns, Hs, ncs, cptrs, C.byref(opt), outs, 0, infos)
     if st != 0 and (raise_on_failure or st not in (B.SS_NOT_CONVERGED, B.SS_BREAKDOWN)):
         ctx.check(st, "steady_state_batched")
@@ -376,7 +382,7 @@ def steady_state(H, c_ops: Sequence, method: str = "iterative-bicgstab", tol: fl
                  precond: str = "ilu0", precision: str = "fp64", maxiter: int = 1000, restart: int = 30,
                  drop_tol: float = 1e-4, fill_factor: float = 10.0, w: float = 0.0, sigma: float = 1e-15,
                  use_rcm: bool = True, seed: int = 0, ctx: Optional[Context] = None, out=None,
-                 raise_on_failure: bool = True, inner_rtol: float = 1e-5):
+                 raise_on_failure: bool = True, inner_rtol: float = 1e-5, lgmres_k: int = 0):
     """rho_ss (d x d complex128, trace one) and the solve's info dict.
 
     out: optional CUDA complex128 tensor of d*d elements (column-major rho);
@@ -388,7 +394,7 @@ def steady_state(H, c_ops: Sequence, method: str = "iterative-bicgstab", tol: fl
     cvs = [_CsrHost(c) for c in c_ops]
     arr = (B.CsrView * max(len(cvs), 1))(*[c.view for c in cvs])
     opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed,
-                   inner_rtol)
+                   inner_rtol, lgmres_k)
     d = hv.view.n_rows
     info = B.Info()
     if out is None:
@@ -414,10 +420,10 @@ class Server:
                  precision: str = "mixed", maxiter: int = 1000, restart: int = 30, drop_tol: float = 1e-4,
                  fill_factor: float = 10.0, w: float = 0.0, sigma: float = 1e-15, use_rcm: bool = True,
                  seed: int = 0, inner_rtol: float = 1e-5, hbm_budget_mb: float = 0.0, max_waves: int = 4,
-                 max_wave_systems: int = 0, device: int = 0):
+                 max_wave_systems: int = 0, device: int = 0, lgmres_k: int = 0):
         lib = B.load()
         opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm,
-                       seed, inner_rtol)
+                       seed, inner_rtol, lgmres_k)
         so = B.ServerOptions()
         lib.ss_server_options_default(C.byref(so))
         so.hbm_budget_mb = hbm_budget_mb

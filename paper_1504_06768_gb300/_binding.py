@@ -17,7 +17,8 @@ SS_OK, SS_ERR_INVALID, SS_ERR_OOM, SS_NOT_CONVERGED, SS_BREAKDOWN, SS_ZERO_PIVOT
 STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "NOT_CONVERGED", 4: "BREAKDOWN",
                 5: "ZERO_PIVOT", 6: "ERR_TIMEOUT", 7: "ERR_CUDA", 8: "ERR_UNSUPPORTED"}
 METHODS = {"direct": 0, "iterative-lgmres": 1, "iterative-gmres": 1, "gmres": 1,
-           "iterative-bicgstab": 2, "bicgstab": 2, "inverse-power": 3}
+           "iterative-bicgstab": 2, "bicgstab": 2, "inverse-power": 3, "auto": 4}
+METHOD_NAMES = {0: "direct", 1: "iterative-lgmres", 2: "iterative-bicgstab", 3: "inverse-power", 4: "auto"}
 PRECONDS = {"ilu0": 0, "ilut": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 KRYLOV = {"bicgstab": 0, "gmres": 1}
@@ -33,7 +34,7 @@ class Options(C.Structure):
     _fields_ = [("method", C.c_int), ("precond", C.c_int), ("precision", C.c_int), ("tol", C.c_double),
                 ("maxiter", C.c_int), ("restart", C.c_int), ("drop_tol", C.c_double),
                 ("fill_factor", C.c_double), ("w", C.c_double), ("sigma", C.c_double),
-                ("use_rcm", C.c_int), ("seed", C.c_uint64), ("inner_rtol", C.c_double)]
+                ("use_rcm", C.c_int), ("seed", C.c_uint64), ("inner_rtol", C.c_double), ("lgmres_k", C.c_int)]
 
 
 class Info(C.Structure):
@@ -41,11 +42,13 @@ class Info(C.Structure):
                 ("resid_Lrho", C.c_double), ("w_used", C.c_double), ("condest", C.c_double),
                 ("n", C.c_int64), ("nnz", C.c_int64), ("bandwidth", C.c_int64), ("profile", C.c_int64),
                 ("nnz_factors", C.c_int64), ("levels_lower", C.c_int32), ("levels_upper", C.c_int32),
-                ("ms_setup", C.c_double), ("ms_solve", C.c_double)]
+                ("ms_setup", C.c_double), ("ms_solve", C.c_double), ("method", C.c_int),
+                ("bw_modified", C.c_int64), ("bw_shifted", C.c_int64)]
 
     def as_dict(self) -> dict:
         out = {k: getattr(self, k) for k, _ in self._fields_}
         out["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
+        out["method_name"] = METHOD_NAMES.get(self.method, str(self.method))
         return out
 
 
@@ -93,6 +96,8 @@ _SIGNATURES = {
     "ss_profile_enable": (C.c_int, [_P, C.c_int]),
     "ss_profile_read": (C.c_int, [_P, C.c_int, _I64P, _DP]),
     "ss_launch_count": (C.c_ulonglong, []),
+    "lgmres_solve": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int, C.c_int, C.c_int,
+                               C.POINTER(C.c_int), _DP]),
     "krylov_solve_noalloc": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int, C.POINTER(C.c_int), _DP]),
     "steady_state": (C.c_int, [_P, C.POINTER(CsrView), C.c_int, C.POINTER(CsrView), C.POINTER(Options),
                                _P, C.c_int, C.POINTER(Info)]),

@@ -142,6 +142,7 @@ extern "C" void ss_options_default(ss_options* o) {
     o->use_rcm = 1;
     o->seed = 0;
     o->inner_rtol = 1e-5;
+    o->lgmres_k = 0;
 }
 
 // ----------------------------------------------------------------- matrices
@@ -432,6 +433,28 @@ extern "C" ss_status krylov_solve(ss_ctx ctx, ss_mat A, ss_prec M, int krylov, c
     return SS_OK;
 }
 
+extern "C" ss_status lgmres_solve(ss_ctx ctx, ss_mat A, ss_prec M, const double* b, double* x, double tol,
+                                  int maxiter, int restart, int augment, int* iters_out, double* resid_out) {
+    SS_TRY(check_ctx(ctx));
+    if (!A || !M || !b || !x) return set_error(ctx, SS_ERR_INVALID, "null argument");
+    if (M->f.n_rows != A->m.n_rows) return set_error(ctx, SS_ERR_INVALID, "preconditioner size mismatch");
+    KrylovWork w;
+    ss_status st = krylov_workspace(ctx, w, A->m.n_rows, SS_KRYLOV_GMRES, restart, augment);
+    KrylovResultHost res;
+    if (st == SS_OK)
+        st = gmres_dev(ctx, A->m, M, w, reinterpret_cast<const double2*>(b), reinterpret_cast<double2*>(x), tol,
+                       maxiter, restart, &res, nullptr, augment);
+    krylov_workspace_free(ctx, w);
+    SS_TRY(st);
+    if (iters_out) *iters_out = res.iters;
+    if (resid_out) *resid_out = res.resid;
+    if (res.status != SS_OK) {
+        ctx->last_error = "iteration cap reached";
+        return (ss_status)res.status;
+    }
+    return SS_OK;
+}
+
 // Steady state of one system (all §-references are to the paper).
 namespace {
 
@@ -503,15 +526,19 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
     ss_options_default(&opt);
     if (opt_in) opt = *opt_in;
     if (!rho_out || !H) return set_error(ctx, SS_ERR_INVALID, "null argument");
-    if (opt.method < SS_METHOD_DIRECT || opt.method > SS_METHOD_INVERSE_POWER)
+    if (opt.method < SS_METHOD_DIRECT || opt.method > SS_METHOD_AUTO)
         return set_error(ctx, SS_ERR_INVALID, "unknown method");
     const bool mixed = opt.precision == SS_PREC_MIXED;
     const bool direct = opt.method == SS_METHOD_DIRECT;
+    const bool automatic = opt.method == SS_METHOD_AUTO;
     if (mixed && opt.method != SS_METHOD_ITER_BICGSTAB)
         return set_error(ctx, SS_ERR_UNSUPPORTED, "mixed precision is built for iterative-bicgstab only");
     if (!(opt.tol > 0.0) || opt.maxiter < 1) return set_error(ctx, SS_ERR_INVALID, "tol must be > 0, maxiter >= 1");
-    const bool power = opt.method == SS_METHOD_INVERSE_POWER;
-    const int krylov = opt.method == SS_METHOD_ITER_GMRES ? SS_KRYLOV_GMRES : SS_KRYLOV_BICGSTAB;
+    if ((opt.method == SS_METHOD_ITER_GMRES || automatic) &&
+        (opt.restart < 1 || opt.lgmres_k < 0 || opt.restart + opt.lgmres_k > KRYLOV_MAX_M))
+        return set_error(ctx, SS_ERR_INVALID, "GMRES needs restart >= 1, lgmres_k >= 0, restart + lgmres_k <= 64");
+    bool power = opt.method == SS_METHOD_INVERSE_POWER;
+    int krylov = opt.method == SS_METHOD_ITER_GMRES || automatic ? SS_KRYLOV_GMRES : SS_KRYLOV_BICGSTAB;
     const double t0 = now_ms();
 
     ss_mat L = nullptr, A = nullptr, Ap = nullptr;
@@ -520,19 +547,52 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
     if (st != SS_OK) return st;
     const int64_t d = L->d, n = L->m.n_rows;
     double w_used = 0.0;
-    if (power) st = add_shift(ctx, L, opt.sigma, &A);
-    else st = add_trace_row(ctx, L, opt.w, &A, &w_used);
+    std::vector<int32_t> perm(n);
+    int64_t bw_mod = 0, bw_shift = 0;
+    bool have_perm = false;
+    if (automatic) {
+        // sections "Results" and "Conclusion": compare the RCM bandwidths of
+        // L~ and L - sigma I; inverse power when the trace row spoils the
+        // reduction (1.5 separates the paper's printed pairs: 139/137 and
+        // 239/229 for GMRES, 405/167 for inverse power)
+        ss_mat Am = nullptr, As = nullptr;
+        std::vector<int32_t> pm(n), ps(n);
+        st = add_trace_row(ctx, L, opt.w, &Am, &w_used);
+        if (st == SS_OK) st = add_shift(ctx, L, opt.sigma, &As);
+        if (st == SS_OK) st = rcm_permute(ctx, Am, pm.data(), &bw_mod, nullptr);
+        if (st == SS_OK) st = rcm_permute(ctx, As, ps.data(), &bw_shift, nullptr);
+        if (st == SS_OK) {
+            power = (double)bw_mod > 1.5 * (double)bw_shift;
+            A = power ? As : Am;
+            ss_mat_free(power ? Am : As);
+            if (power) w_used = 0.0;
+            perm.swap(power ? ps : pm);
+            have_perm = opt.use_rcm != 0;
+        } else {
+            ss_mat_free(Am);
+            ss_mat_free(As);
+        }
+    } else if (power) {
+        st = add_shift(ctx, L, opt.sigma, &A);
+    } else {
+        st = add_trace_row(ctx, L, opt.w, &A, &w_used);
+    }
     ss_mat_free(L);
     if (st != SS_OK) return st;
 
-    std::vector<int32_t> perm(n);
-    if (opt.use_rcm) st = rcm_permute(ctx, A, perm.data(), nullptr, nullptr);
-    else for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+    if (!have_perm) {
+        if (opt.use_rcm) st = rcm_permute(ctx, A, perm.data(), nullptr, nullptr);
+        else for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+    }
     if (st == SS_OK) st = permute(ctx, A, perm.data(), &Ap);
     ss_mat_free(A);
     if (st != SS_OK) return st;
 
     ss_info inf{};
+    inf.method = automatic ? (power ? SS_METHOD_INVERSE_POWER : SS_METHOD_ITER_GMRES) : opt.method;
+    inf.bw_modified = bw_mod;
+    inf.bw_shifted = bw_shift;
+    const int kaug = krylov == SS_KRYLOV_GMRES ? opt.lgmres_k : 0;
     inf.n = n;
     inf.nnz = Ap->m.nnz;
     inf.w_used = w_used;
@@ -572,7 +632,7 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
     SS_CUDA(ctx, cudaMemcpyAsync(perm_d, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
     SS_CUDA(ctx, cudaMemcpyAsync(tidx_d, tidx.data(), sizeof(int32_t) * d, cudaMemcpyHostToDevice, ctx->stream));
     STEP(su_condest(ctx, M, n, y, x, scr, &inf.condest));
-    STEP(krylov_workspace(ctx, kw, n, krylov, krylov == SS_KRYLOV_GMRES ? opt.restart : 0));
+    STEP(krylov_workspace(ctx, kw, n, krylov, krylov == SS_KRYLOV_GMRES ? opt.restart : 0, kaug));
     const double t1 = now_ms();
 
     double lr = INFINITY;
@@ -621,7 +681,7 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
         for (int pass = 0; pass < 8; ++pass) {
             int left = opt.maxiter - total;
             if (krylov == SS_KRYLOV_GMRES)
-                STEP(gmres_dev(ctx, Ap->m, M, kw, b, x, inner, left, opt.restart, &res));
+                STEP(gmres_dev(ctx, Ap->m, M, kw, b, x, inner, left, opt.restart, &res, nullptr, kaug));
             else
                 STEP(bicgstab_dev(ctx, Ap->m, M, kw, b, x, inner, left, &res));
             total += res.iters;
@@ -655,7 +715,7 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
             if (outer > 1) std::swap(b, x);        // b <- the latest normalised iterate
             STEP(su_zero(ctx, n, x));
             if (krylov == SS_KRYLOV_GMRES)
-                STEP(gmres_dev(ctx, Ap->m, M, kw, b, x, 0.1 * opt.tol, opt.maxiter, opt.restart, &res, &oc));
+                STEP(gmres_dev(ctx, Ap->m, M, kw, b, x, 0.1 * opt.tol, opt.maxiter, opt.restart, &res, &oc, kaug));
             else
                 STEP(bicgstab_dev(ctx, Ap->m, M, kw, b, x, 0.1 * opt.tol, opt.maxiter, &res, &oc));
             total += res.iters;

@@ -537,6 +537,7 @@ ss_status wave_end(BatchWave& w, ss_info* infos) {
             ss_info& inf = infos[q];
             std::memset(&inf, 0, sizeof(inf));
             inf.status = w.hs[q].status;
+            inf.method = SS_METHOD_ITER_BICGSTAB;
             inf.iters = w.hs[q].iters;
             inf.outer_iters = w.hs[q].outer;
             inf.resid_Lrho = w.hs[q].resid;

@@ -1,7 +1,9 @@
 // Right-preconditioned Krylov solvers on the device (section "Iterative
 // solvers"): BiCGSTAB (van der Vorst 1992) and restarted GMRES(m) (Saad and
 // Schultz 1986), solving A M^{-1} u = b, x = M^{-1} u, so that the updated
-// residual is the residual of A x = b itself.
+// residual is the residual of A x = b itself.  GMRES optionally augments each
+// cycle with the corrections of the k previous cycles (LGMRES(m, k), Baker,
+// Jessup and Manteuffel 2005).
 //
 // All scalars live in device memory (KrylovState) and every reduction is a
 // deterministic two-stage sum: each block writes its partial sums, the last
@@ -333,8 +335,9 @@ __global__ void gm_orth_update(int64_t n, const double2* __restrict__ V, int64_t
     }
 }
 
-// H[j+1, j] = ||w||; Givens rotations; residual estimate; end of cycle -> y
-__global__ void gm_norm(int64_t n, const double2* __restrict__ w, int j, KrylovState* st) {
+// H[j+1, j] = ||w||; Givens rotations; residual estimate; end of cycle -> y.
+// mt = the cycle's dimension (restart length + augmentation vectors in use).
+__global__ void gm_norm(int64_t n, const double2* __restrict__ w, int j, int mt, KrylovState* st) {
     if (st->halt) return;
     double2 acc[1] = {d2(0, 0)};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -375,7 +378,7 @@ __global__ void gm_norm(int64_t n, const double2* __restrict__ w, int j, KrylovS
     st->iters += 1;
     double res = hypot(st->g[j + 1].x, st->g[j + 1].y);
     st->rnorm = res;
-    bool end = res <= st->tol || st->iters >= st->maxiter || j + 1 >= st->m || (rr.x == 0.0 && rr.y == 0.0) || hn == 0.0;
+    bool end = res <= st->tol || st->iters >= st->maxiter || j + 1 >= mt || (rr.x == 0.0 && rr.y == 0.0) || hn == 0.0;
     if (end) {
         const int k = j + 1;
         for (int i = k - 1; i >= 0; --i) {   // back substitution H y = g
@@ -399,20 +402,47 @@ __global__ void gm_update_x(int64_t n, const double2* __restrict__ Z, int64_t ld
     }
 }
 
+// LGMRES end of cycle: dx = sum_{i<k} y_i Z_i, x += dx, dnorm = ||dx||
+__global__ void lg_update_x(int64_t n, const double2* __restrict__ Z, int64_t ldz, double2* __restrict__ x,
+                            double2* __restrict__ dx, KrylovState* st) {
+    if (st->done) return;
+    const int k = st->k;
+    double2 acc[1] = {d2(0, 0)};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 di = d2(0, 0);
+        for (int l = 0; l < k; ++l) di = cadd(di, cmul(st->y[l], Z[(int64_t)l * ldz + i]));
+        dx[i] = di;
+        x[i] = cadd(x[i], di);
+        acc[0].x += cabs2(di);
+    }
+    if (reduce_last_block<1>(acc, st->partials, &st->counter)) st->dnorm = sqrt(acc[0].x);
+}
+
+// LGMRES: the normalised correction replaces the oldest stored one (slot)
+__global__ void lg_store(int64_t n, const double2* __restrict__ dx, double2* __restrict__ slot, const KrylovState* st) {
+    if (st->done || !(st->dnorm > 0.0)) return;
+    const double inv = 1.0 / st->dnorm;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        slot[i] = cscale(dx[i], inv);
+}
+
 
 }  // namespace
 
 // ------------------------------------------------------------------ host
 
-ss_status krylov_workspace(ss_ctx ctx, KrylovWork& w, int64_t n, int method, int m) {
+ss_status krylov_workspace(ss_ctx ctx, KrylovWork& w, int64_t n, int method, int m, int kaug) {
+    if (method == SS_KRYLOV_GMRES && (m < 1 || kaug < 0 || m + kaug > KRYLOV_MAX_M))
+        return set_error(ctx, SS_ERR_INVALID, "GMRES needs restart >= 1, augmentation >= 0, restart + augmentation <= 64");
     w.n = n;
     w.method = method;
     w.m = m;
+    w.kaug = method == SS_KRYLOV_GMRES ? kaug : 0;
     const int nb = red_blocks(n);
     SS_TRY(dev_alloc_n(ctx, &w.st, 1));
     SS_TRY(dev_alloc_n(ctx, &w.partials, (size_t)nb * 32));
     SS_CUDA(ctx, cudaMemsetAsync(w.st, 0, sizeof(KrylovState), ctx->stream));
-    size_t nvec = method == SS_KRYLOV_GMRES ? (size_t)(2 * m + 2) : 8;
+    size_t nvec = method == SS_KRYLOV_GMRES ? (size_t)(2 * (m + kaug) + 1 + (kaug > 0 ? 1 : 0)) : 8;
     SS_TRY(dev_alloc_n(ctx, &w.vecs, nvec * (size_t)n));
     w.nvec = nvec;
     SS_CUDA(ctx, cudaHostAlloc(reinterpret_cast<void**>(&w.host_st), sizeof(KrylovState), cudaHostAllocDefault));
@@ -533,46 +563,61 @@ ss_status bicgstab_dev32(ss_ctx ctx, const DeviceCSR& A, const float2* val32, ss
 }
 
 ss_status gmres_dev(ss_ctx ctx, const DeviceCSR& A, ss_prec M, KrylovWork& w, const double2* b, double2* x, double tol,
-                    int maxiter, int m, KrylovResultHost* out, const OuterCheck* oc) {
+                    int maxiter, int m, KrylovResultHost* out, const OuterCheck* oc, int kaug) {
     const int64_t n = A.n_rows;
-    if (m < 1 || m > KRYLOV_MAX_M) return set_error(ctx, SS_ERR_INVALID, "GMRES restart must be in 1..64");
-    double2* V = w.vecs;                       // m + 1 basis vectors
-    double2* Z = V + (size_t)(m + 1) * n;      // m preconditioned vectors
-    double2* rv = V + (size_t)m * n;           // v_m doubles as the restart residual buffer
+    if (m < 1 || kaug < 0 || m + kaug > KRYLOV_MAX_M)
+        return set_error(ctx, SS_ERR_INVALID, "GMRES needs restart >= 1, augmentation >= 0, restart + augmentation <= 64");
+    if (w.method != SS_KRYLOV_GMRES || w.m != m || w.kaug != kaug || w.n != n)
+        return set_error(ctx, SS_ERR_INVALID, "GMRES workspace made for another restart length or augmentation");
+    const int mx = m + kaug;
+    double2* V = w.vecs;                        // mx + 1 basis vectors
+    double2* Z = V + (size_t)(mx + 1) * n;      // mx search directions: m preconditioned, then the stored corrections
+    double2* D = Z + (size_t)mx * n;            // this cycle's correction (kaug > 0)
+    double2* rv = V + (size_t)m * n;            // v_m doubles as the restart residual buffer
     const int nb = red_blocks(n);
     const unsigned eg = (unsigned)std::min<int64_t>(grid_for(n, RED_THREADS), 4 * std::max(ctx->num_sms, 1));
     int* halt = &w.st->halt;
-    SS_TRY(set_params(ctx, w, tol, maxiter, m));
+    int stored = 0, oldest = 0;                 // corrections held in Z[m .. m + stored)
+    SS_TRY(set_params(ctx, w, tol, maxiter, mx));
     while (true) {
         // restart: y = A x into V_1 as scratch, r into V_m, v_0 = r / beta
         { ProfScope ps_(ctx, PROF_SPMV); spmv_launch(A, x, V + n, nullptr, ctx->stream); }
         gm_restart<<<(ss_count_launch(), nb), RED_THREADS, 0, ctx->stream>>>(n, b, V + n, rv, w.st);
         gm_scale<<<(ss_count_launch(), eg), RED_THREADS, 0, ctx->stream>>>(n, rv, V, w.st);
-        for (int j = 0; j < m; ++j) {
+        const int mt = m + stored;
+        for (int j = 0; j < mt; ++j) {
             double2* vj = V + (size_t)j * n;
             double2* zj = Z + (size_t)j * n;
             double2* wv = V + (size_t)(j + 1) * n;
-            SS_TRY(prec_apply_dev(ctx, M, vj, zj, halt));
+            if (j < m) SS_TRY(prec_apply_dev(ctx, M, vj, zj, halt));     // else zj is a stored correction
             { ProfScope ps_(ctx, PROF_SPMV); spmv_launch(A, zj, wv, halt, ctx->stream); }
             for (int pass = 0; pass < 2; ++pass) {      // classical Gram-Schmidt, twice
                 for (int base = 0; base <= j; base += 8)
                     gm_dots<8><<<(ss_count_launch(), nb), RED_THREADS, 0, ctx->stream>>>(n, V, n, j, base, wv, w.st, pass);
                 gm_orth_update<<<(ss_count_launch(), eg), RED_THREADS, 0, ctx->stream>>>(n, V, n, j, wv, w.st);
             }
-            gm_norm<<<(ss_count_launch(), nb), RED_THREADS, 0, ctx->stream>>>(n, wv, j, w.st);
+            gm_norm<<<(ss_count_launch(), nb), RED_THREADS, 0, ctx->stream>>>(n, wv, j, mt, w.st);
             gm_scale<<<(ss_count_launch(), eg), RED_THREADS, 0, ctx->stream>>>(n, wv, wv, w.st);
         }
-        gm_update_x<<<(ss_count_launch(), eg), RED_THREADS, 0, ctx->stream>>>(n, Z, n, x, w.st);
+        int slot = -1;
+        if (kaug > 0) {
+            slot = m + (stored < kaug ? stored : oldest);
+            lg_update_x<<<(ss_count_launch(), nb), RED_THREADS, 0, ctx->stream>>>(n, Z, n, x, D, w.st);
+            lg_store<<<(ss_count_launch(), eg), RED_THREADS, 0, ctx->stream>>>(n, D, Z + (size_t)slot * n, w.st);
+        } else {
+            gm_update_x<<<(ss_count_launch(), eg), RED_THREADS, 0, ctx->stream>>>(n, Z, n, x, w.st);
+        }
         SS_CUDA(ctx, cudaGetLastError());
         SS_TRY(read_state(ctx, w));
         if (w.host_st->done) break;
+        if (slot >= 0 && w.host_st->dnorm > 0.0) {
+            if (stored < kaug) ++stored;
+            else oldest = (oldest + 1) % kaug;
+        }
         bool met = false;
         SS_TRY(outer_met(ctx, oc, x, &met));
         if (met) { w.host_st->status = SS_OK; break; }
-        if (w.host_st->iters >= maxiter) {
-            // the cycle ended on the iteration cap: one more restart pass sets the status
-            continue;
-        }
+        // a cycle that ended on the iteration cap: the next restart pass sets the status
     }
     SS_TRY(prec_check_error(ctx, M));
     out->status = w.host_st->status;

@@ -3,7 +3,7 @@
 
 #include "common.cuh"
 
-constexpr int KRYLOV_MAX_M = 64;   // largest GMRES restart length
+constexpr int KRYLOV_MAX_M = 64;   // largest GMRES cycle dimension (restart length + augmentation vectors)
 
 struct KrylovState {
     // parameters
@@ -21,6 +21,7 @@ struct KrylovState {
     int k;                          // GMRES: inner steps in the current cycle
     // scalars
     double rnorm, snorm, rhat_norm, hnorm;
+    double dnorm;                   // LGMRES: ||Z y|| of the last cycle's correction
     double2 rho, alpha, omega, beta;
     // GMRES
     double2 H[(KRYLOV_MAX_M + 1) * KRYLOV_MAX_M];   // row-major (i, j) at i * M + j
@@ -35,6 +36,7 @@ struct KrylovWork {
     int64_t n = 0;
     int method = 0;
     int m = 0;
+    int kaug = 0;
     KrylovState* st = nullptr;
     KrylovState* host_st = nullptr;     // pinned mirror
     double2* partials = nullptr;
@@ -62,12 +64,17 @@ struct OuterCheck {
     double tol = 0.0;
 };
 
-ss_status krylov_workspace(ss_ctx ctx, KrylovWork& w, int64_t n, int method, int m);
+// GMRES workspace: m + kaug + 1 basis vectors, m + kaug search directions
+// (the last kaug hold LGMRES's stored corrections) and, with kaug > 0, one
+// correction vector.
+ss_status krylov_workspace(ss_ctx ctx, KrylovWork& w, int64_t n, int method, int m, int kaug = 0);
 void krylov_workspace_free(ss_ctx ctx, KrylovWork& w);
 ss_status bicgstab_dev(ss_ctx ctx, const DeviceCSR& A, ss_prec M, KrylovWork& w, const double2* b, double2* x,
                        double tol, int maxiter, KrylovResultHost* out, const OuterCheck* oc = nullptr);
 // FP32 BiCGSTAB (inner solve of the mixed path): A's FP32 values, M's FP32 factors.
 ss_status bicgstab_dev32(ss_ctx ctx, const DeviceCSR& A, const float2* val32, ss_prec M, KrylovWork& w,
                          const float2* b, float2* x, double tol, int maxiter, KrylovResultHost* out);
+// Restarted GMRES(m), or LGMRES(m, kaug) for kaug > 0 (the workspace must
+// have been made with the same m and kaug).
 ss_status gmres_dev(ss_ctx ctx, const DeviceCSR& A, ss_prec M, KrylovWork& w, const double2* b, double2* x, double tol,
-                    int maxiter, int m, KrylovResultHost* out, const OuterCheck* oc = nullptr);
+                    int maxiter, int m, KrylovResultHost* out, const OuterCheck* oc = nullptr, int kaug = 0);

@@ -29,7 +29,7 @@ def lib():
 def test_header_parses():
     names = _declared_functions()
     for must in ("assemble_liouvillian", "rcm_permute", "ilu_factor", "steady_state", "add_trace_row",
-                 "add_shift", "permute", "krylov_solve", "spmv", "precond_apply", "ss_ctx_create"):
+                 "add_shift", "permute", "krylov_solve", "lgmres_solve", "spmv", "precond_apply", "ss_ctx_create"):
         assert must in names
 
 
@@ -65,9 +65,12 @@ def test_options_defaults(lib):
     import ctypes
     from paper_1504_06768_gb300 import _binding as B
     o = B.Options()
+    o.lgmres_k, o.inner_rtol = 77, 9.0            # the last fields: written at the offsets the header gives
     lib.ss_options_default(ctypes.byref(o))
     assert (o.method, o.precond, o.precision, o.maxiter, o.restart, o.use_rcm) == (2, 0, 0, 1000, 30, 1)
     assert o.tol == 1e-10 and o.sigma == 1e-15 and o.drop_tol == 1e-4 and o.fill_factor == 10.0
+    assert o.inner_rtol == 1e-5 and o.lgmres_k == 0
+    assert B.METHODS["auto"] == 4 and B.METHOD_NAMES[B.METHODS["iterative-lgmres"]] == "iterative-lgmres"
 
 
 def test_csr_marshalling_sorts_and_keeps_arrays():

@@ -454,3 +454,107 @@ def test_direct_closed_form_coherent_state(ss):
     n = np.arange(30)
     psi = np.exp(-abs(alpha) ** 2 / 2) * alpha ** n / np.sqrt(np.array([float(factorial(int(k))) for k in n]))
     assert trace_distance(rho, np.outer(psi, psi.conj())) <= 1e-12
+
+
+# ------------------------------------------------------------------ LGMRES
+
+@pytest.mark.parametrize("m,k,cycles", [(10, 3, 3), (10, 3, 6), (6, 2, 8), (20, 0, 2)])
+def test_lgmres_iterates_match_oracle_after_fixed_cycles(ss, m, k, cycles):
+    """Unconverged iterates after a fixed number of LGMRES(m, k) cycles
+    (tol = 0, maxiter = the Arnoldi steps of those cycles): the device's
+    classical Gram-Schmidt and the oracle's modified Gram-Schmidt span the
+    same spaces, so x agrees to rounding (the oracle's iterates move by
+    ~1e-14 under perturbations of the inputs at rounding level)."""
+    from oracle.krylov import lgmres
+    s = jaynes_cummings_rwa(seed=1, N=8)
+    L = liouvillian_sparse(s.H, s.c_ops)
+    A, b = modified_liouvillian(L, s.d, default_weight(L))
+    p = rcm_order(A)
+    Aq = permute_symmetric(A, p)
+    F = oilu.ilu0(Aq)
+    ref = lgmres(lambda v: Aq @ v, lambda r: oilu.precond_apply_fast(F, r), b[p], None, 0.0, restart=m, augment=k,
+                 maxiter=10**6, max_cycles=cycles)
+    Ad, w = ss.add_trace_row(ss.assemble_liouvillian(s.H, s.c_ops))
+    perm, _, _ = ss.rcm_permute(Ad)
+    assert np.array_equal(perm, p)
+    Ap = ss.permute(Ad, perm)
+    M = ss.ilu_factor(Ap, "ilu0")
+    bg = np.zeros(Ap.shape[0], dtype=complex)
+    bg[np.flatnonzero(perm == 0)[0]] = w
+    steps = sum(m + min(c, k) for c in range(cycles))
+    x, st, it, res = ss.krylov_solve(Ap, M, _dev(bg), method="lgmres", restart=m, augment=k, tol=0.0, maxiter=steps)
+    assert st == 3 and it == steps == ref.iters
+    x = x.cpu().numpy()
+    assert np.linalg.norm(x - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+    assert np.linalg.norm(bg - Aq @ x) == pytest.approx(np.linalg.norm(b[p] - Aq @ ref.x), rel=1e-6)
+
+
+def test_lgmres_solves_trace_row_system(ss):
+    s = SMALL_SYSTEMS["kerr17"]()
+    Ad, w = ss.add_trace_row(ss.assemble_liouvillian(s.H, s.c_ops))
+    perm, _, _ = ss.rcm_permute(Ad)
+    Ap = ss.permute(Ad, perm)
+    M = ss.ilu_factor(Ap, "ilu0")
+    b = np.zeros(Ap.shape[0], dtype=complex)
+    b[np.flatnonzero(perm == 0)[0]] = w
+    x, st, it, res = ss.krylov_solve(Ap, M, _dev(b), method="lgmres", restart=8, augment=3, tol=1e-13 * w)
+    assert st == 0 and res <= 1e-13 * w
+    L = liouvillian_sparse(s.H, s.c_ops)
+    A, bo = modified_liouvillian(L, s.d, default_weight(L))
+    xo = np.empty_like(b)
+    xo[perm] = x.cpu().numpy()                       # back to natural order
+    ref = np.linalg.solve(A.toarray(), bo)
+    assert np.max(np.abs(xo - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+def test_lgmres_rejects_bad_dimensions(ss):
+    s = SMALL_SYSTEMS["cavity"]()
+    with pytest.raises(ss.SolverError) as e:
+        ss.steady_state(s.H, s.c_ops, method="iterative-lgmres", restart=60, lgmres_k=5)
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("name", ["cavity_thermal", "jc8", "kerr17"])
+def test_steady_state_lgmres_matches_dense(ss, name):
+    s = SMALL_SYSTEMS[name]()
+    rho, info = ss.steady_state(s.H, s.c_ops, method="iterative-lgmres", restart=10, lgmres_k=3, tol=1e-12)
+    assert info["status"] == 0 and info["method_name"] == "iterative-lgmres"
+    assert trace_distance(rho, steady_state_dense(s.H, s.c_ops)) <= 1e-10
+
+
+def test_steady_state_config2_jc40_lgmres(ss):
+    s = jaynes_cummings_rwa(seed=7)
+    rho, info = ss.steady_state(s.H, s.c_ops, method="iterative-lgmres", precond="ilu0", restart=30, lgmres_k=3,
+                                tol=1e-12)
+    assert info["n"] == 6400 and info["status"] == 0
+    assert trace_distance(rho, _dense_ref(7)) <= 1e-10
+
+
+# ------------------------------------------------------ method selection
+
+def test_auto_selection_on_the_papers_systems(ss):
+    """The RCM bandwidths the rule compares are the ones printed in Fig. 1 and
+    Fig. 3, and the choice is the oracle's (GMRES on L~ for the
+    Jaynes-Cummings and optomechanical models, inverse power for the 5-spin
+    chain).  Only the choice is checked here (maxiter 5)."""
+    import json
+    import os
+    from oracle.krylov import select_method
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_rcm_bandwidth_profile.json")))
+    B = {(c["system"], c["matrix"]): c["B"] for c in gold["cases"]}
+    names = {"gmres": "iterative-lgmres", "power-gmres": "inverse-power"}
+    for key, maker in (("jc", paper_jc_nonrwa), ("spin", paper_spin_chain), ("opto", paper_optomechanics)):
+        s = maker()
+        _, info = ss.steady_state(s.H, s.c_ops, method="auto", maxiter=5, raise_on_failure=False)
+        assert (info["bw_modified"], info["bw_shifted"]) == (B[(key, "modified")], B[(key, "shifted")])
+        assert info["method_name"] == names[select_method(s.H, s.c_ops)[0]], key
+
+
+@pytest.mark.parametrize("maker,expect", [(lambda: paper_spin_chain(), "inverse-power"),
+                                          (lambda: driven_cavity(n_th=0.2), "iterative-lgmres")],
+                         ids=["spin5", "cavity"])
+def test_auto_steady_state_matches_dense(ss, maker, expect):
+    s = maker()
+    rho, info = ss.steady_state(s.H, s.c_ops, method="auto", lgmres_k=3, tol=1e-10)
+    assert info["status"] == 0 and info["method_name"] == expect and info["resid_Lrho"] <= 1e-10
+    assert trace_distance(rho, steady_state_dense(s.H, s.c_ops)) <= 1e-8

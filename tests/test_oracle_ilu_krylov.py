@@ -9,7 +9,7 @@ import scipy.linalg as la
 import scipy.sparse as sp
 
 from oracle import ilu
-from oracle.krylov import BREAKDOWN, NOT_CONVERGED, OK, bicgstab, gmres, steady_state_iterative
+from oracle.krylov import BREAKDOWN, NOT_CONVERGED, OK, bicgstab, gmres, lgmres, select_method, steady_state_iterative
 from oracle.metrics import trace_distance
 from oracle.rng import splitmix64, start_vector
 from oracle.steady import steady_state_dense
@@ -213,3 +213,112 @@ def test_start_vector_counters():
     G = 0x9E3779B97F4A7C15
     z = splitmix64(42 + 7 * G)                          # counter 6 = element 3, real part
     assert v[3].real == 2.0 * ((z >> 11) * 2.0 ** -53) - 1.0
+
+
+# ------------------------------------------------------------------ LGMRES
+
+def _scipy_lgmres_cycles(op, b, m, k, cycles):
+    """SciPy's independent LGMRES, unpreconditioned, run for exactly `cycles`
+    restart cycles (a vanishing tolerance never ends a cycle early)."""
+    from scipy.sparse.linalg import lgmres as sp_lgmres
+    x, info = sp_lgmres(op, b, rtol=1e-300, atol=0.0, maxiter=cycles, inner_m=m, outer_k=k)
+    assert info == cycles
+    return x
+
+
+@pytest.mark.parametrize("m,k", [(6, 2), (8, 3)])
+def test_lgmres_matches_scipy_unpreconditioned(m, k):
+    """With M = I, every cycle minimises over the same space as SciPy's
+    LGMRES (Krylov directions of the restart residual plus the stored
+    corrections), so the iterates agree after any number of cycles."""
+    A = _rand_sparse(80, 0.06, 3, dominance=0.6)
+    b = np.random.default_rng(3).standard_normal(80) + 0.3j
+    for cycles in (1, 2, 5):
+        ours = lgmres(lambda v: A @ v, lambda r: r, b, None, 0.0, restart=m, augment=k, maxiter=10**6,
+                      max_cycles=cycles)
+        ref = _scipy_lgmres_cycles(A, b, m, k, cycles)
+        assert np.linalg.norm(ours.x - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert ours.resid > 1e-8 * np.linalg.norm(b)          # still short of convergence: iterates carry the method
+
+
+def test_lgmres_right_preconditioned_matches_scipy_on_a_minv():
+    """Right preconditioning: the cycle space M^{-1} K_m(A M^{-1}, r) + span{dx_i}
+    equals M^{-1} applied to the space SciPy's unpreconditioned LGMRES builds
+    for the operator A M^{-1}, so x = M^{-1} u after each cycle."""
+    from scipy.sparse.linalg import LinearOperator
+    s = kerr_oscillator(10, -0.7, 0.3, 1.1)
+    from oracle.liouvillian import default_weight, liouvillian_sparse, modified_liouvillian
+    L = liouvillian_sparse(s.H, s.c_ops)
+    A, b = modified_liouvillian(L, s.d, default_weight(L))
+    A = sp.csr_matrix(A)
+    A.sort_indices()
+    F = ilu.ilut(A, drop_tol=5e-2, fill_factor=1.0)              # a deliberately rough M
+    minv = lambda r: ilu.precond_apply_fast(F, r)                 # noqa: E731
+    n = A.shape[0]
+    op = LinearOperator((n, n), matvec=lambda u: A @ minv(u), dtype=np.complex128)
+    for cycles in (1, 3, 4):
+        ours = lgmres(lambda v: A @ v, minv, b, None, 0.0, restart=5, augment=2, maxiter=10**6,
+                      max_cycles=cycles)
+        ref = minv(_scipy_lgmres_cycles(op, b, 5, 2, cycles))
+        assert np.linalg.norm(ours.x - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert ours.resid > 1e-10 * np.linalg.norm(b)
+
+
+def test_lgmres_without_augmentation_is_gmres():
+    A = _rand_sparse(120, 0.05, 4)
+    b = np.random.default_rng(4).standard_normal(120) + 0.1j
+    F = ilu.ilut(A, drop_tol=0.3, fill_factor=1.0)                # rough M: several restart cycles
+    ps = lambda r: ilu.precond_apply_fast(F, r)                   # noqa: E731
+    a = lgmres(lambda v: A @ v, ps, b, None, 1e-12, restart=7, augment=0)
+    g = gmres(lambda v: A @ v, ps, b, None, 1e-12, restart=7)
+    assert a.status == g.status == OK and a.iters == g.iters
+    np.testing.assert_allclose(a.x, g.x, rtol=0, atol=1e-13)
+
+
+def test_lgmres_cycle_residuals_never_increase():
+    """Each cycle minimises over a space that contains the zero correction."""
+    A = _rand_sparse(150, 0.04, 5, dominance=0.4)
+    b = np.ones(150, dtype=complex)
+    prev = np.linalg.norm(b)
+    x = None
+    for _ in range(6):
+        res = lgmres(lambda v: A @ v, lambda r: r, b, x, 0.0, restart=5, augment=3, maxiter=10**6,
+                     max_cycles=1)
+        x = res.x
+        rn = np.linalg.norm(b - A @ x)
+        assert rn <= prev * (1 + 1e-12)
+        prev = rn
+
+
+@pytest.mark.parametrize("maker", [lambda: driven_cavity(n_th=0.2), lambda: jaynes_cummings_rwa(seed=1, N=8)],
+                         ids=["cavity", "jc8"])
+def test_lgmres_steady_state_matches_dense(maker):
+    s = maker()
+    res = steady_state_iterative(s.H, s.c_ops, method="lgmres", augment=3, restart=10, tol=1e-12)
+    assert res.status == OK and res.resid_Lrho <= 1e-12
+    assert trace_distance(steady_state_dense(s.H, s.c_ops), res.rho) < 1e-10
+
+
+# ------------------------------------------------------- method selection
+
+def test_select_method_on_the_papers_printed_bandwidths():
+    """Fig. 1 and Fig. 3 print the RCM bandwidths of L - sigma I and L~ for
+    the three model systems; the selection rule reads them: GMRES on L~ for
+    the Jaynes-Cummings and optomechanical models (bandwidth nearly
+    unchanged), inverse power for the 5-spin chain (bandwidth 2.4x)."""
+    from workloads import paper_jc_nonrwa, paper_optomechanics, paper_spin_chain
+    gold = json.load(open(os.path.join(GOLD, "paper_rcm_bandwidth_profile.json")))["cases"]
+    B = {(c["system"], c["matrix"]): c["B"] for c in gold}
+    expect = {"jc": "gmres", "spin": "power-gmres", "opto": "gmres"}
+    for name, maker in (("jc", paper_jc_nonrwa), ("spin", paper_spin_chain), ("opto", paper_optomechanics)):
+        s = maker()
+        method, bm, bs = select_method(s.H, s.c_ops)
+        assert (bm, bs) == (B[(name, "modified")], B[(name, "shifted")])
+        assert method == expect[name], name
+
+
+def test_auto_steady_state_matches_dense():
+    s = driven_cavity(n_th=0.2)
+    res = steady_state_iterative(s.H, s.c_ops, method="auto", tol=1e-12, augment=2)
+    assert res.status == OK
+    assert trace_distance(steady_state_dense(s.H, s.c_ops), res.rho) < 1e-10
