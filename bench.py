@@ -365,18 +365,18 @@ def run_gpu(args):
 
 # ------------------------------------------------ SpMV roofline and serving
 
-def spmv_measure(ss, B, ctx, stream, reps: int = 20):
-    """SpMV of the RCM-ordered trace-row Liouvillian of the 3-site Kerr chain
-    (cutoff 12 per site: n = 2,985,984, nnz = 41.5M, far larger than L2) in
-    FP64 and FP32, timed with CUDA events on the solver's stream.  Bytes: the
-    CSR once (values + int32 columns + row pointers) and x, y once each."""
-    import ctypes as C
-    import torch
-    from workloads import kerr_chain
-    s = kerr_chain()
+def _rcm_trace_row(ss, s):
     A, _ = ss.add_trace_row(ss.assemble_liouvillian(s.H, s.c_ops))
     perm, _, _ = ss.rcm_permute(A)
-    Ap = ss.permute(A, perm)
+    return ss.permute(A, perm)
+
+
+def _time_spmv(ss, B, ctx, stream, Ap, reps):
+    """FP64 and FP32 SpMV of Ap, timed with CUDA events on the solver's
+    stream.  Bytes: the CSR once (values + int32 columns + row pointers) and
+    x, y once each."""
+    import ctypes as C
+    import torch
     n, nnz = Ap.shape[0], Ap.nnz
     lib = B.load()
     x = torch.randn(n, dtype=torch.complex128, device="cuda")
@@ -384,7 +384,7 @@ def spmv_measure(ss, B, ctx, stream, reps: int = 20):
     x32 = x.to(torch.complex64)
     y32 = torch.empty_like(x32)
     peak, kind = _peaks()
-    res = {"matrix": "3-site Kerr chain trace-row Liouvillian, RCM order", "n": n, "nnz": nnz}
+    res = {"n": n, "nnz": nnz}
     for name, fn, vb in (("fp64", lambda: lib.spmv(ctx.handle, Ap.handle, C.c_void_p(x.data_ptr()),
                                                     C.c_void_p(y.data_ptr())), 16),
                          ("fp32", lambda: lib.spmv_f32(ctx.handle, Ap.handle, C.c_void_p(x32.data_ptr()),
@@ -406,6 +406,23 @@ def spmv_measure(ss, B, ctx, stream, reps: int = 20):
     # FP64 complex SpMV does 4 DFMA per stored entry; GB300 runs FP64 FMA at
     # about 1.26 TFLOP/s (measured), so that form is bound by the FP64 pipe
     res["fp64"]["fp64_tflops"] = 8.0 * nnz / (res["fp64"]["us"] * 1e-6) / 1e12
+    return res, x, x32
+
+
+def spmv_measure(ss, B, ctx, stream, reps: int = 20):
+    """SpMV of two RCM-ordered trace-row Liouvillians far larger than L2: the
+    3-site Kerr chain (cutoff 12 per site: n = 2,985,984, nnz = 41.5M) and
+    the optomechanical system scaled to 10 x 160 levels (n = 2,560,000, nnz =
+    28.1M), in FP64 and FP32; then M^{-1} r with the chain's iLU(0) factors."""
+    import ctypes as C
+    import torch
+    from workloads import kerr_chain, optomechanics
+    lib = B.load()
+    peak, kind = _peaks()
+    Ap = _rcm_trace_row(ss, kerr_chain())
+    t, x, x32 = _time_spmv(ss, B, ctx, stream, Ap, reps)
+    res = {"matrix": "3-site Kerr chain trace-row Liouvillian, RCM order", **t}
+    n, nnz = Ap.shape[0], Ap.nnz
     # M^{-1} r with the chain's iLU(0) factors (level-scheduled triangular
     # solves, lower then upper): bytes = factors once (value + column) and
     # the vectors and per-row arrays of both solves
@@ -432,6 +449,10 @@ def spmv_measure(ss, B, ctx, stream, reps: int = 20):
         trsv[name] = {"us": 1000.0 * ms, "bytes": bytes_, "GB/s": gbs, "frac_hbm": gbs / peak}
     trsv["levels"] = [M.info()["levels_lower"], M.info()["levels_upper"]]
     res["ilu0_apply"] = trsv
+    del M, Ap, x, x32, z, z32
+    Aq = _rcm_trace_row(ss, optomechanics(seed=0, Nc=10, Nm=160))
+    t, _, _ = _time_spmv(ss, B, ctx, stream, Aq, reps)
+    res["optomechanics_10x160"] = {"matrix": "optomechanics (10 x 160 levels) trace-row Liouvillian, RCM order", **t}
     return res
 
 
