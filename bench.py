@@ -117,8 +117,27 @@ class ClockSampler:
 
 
 def _systems(rank: int, batch: int):
+    """Rank r solves seeds r*batch .. r*batch+batch-1: replicas share no system."""
     from workloads import jaynes_cummings_rwa
     return [jaynes_cummings_rwa(seed=rank * batch + s, N=JC_N) for s in range(batch)]
+
+
+def _max_over_ranks(x: float, device) -> float:
+    """The largest of the ranks' values (a step of the job lasts as long as
+    its slowest rank); x itself on one rank."""
+    ws, _, _ = _dist()
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_value(ws: int, batch: int, ms_step: float) -> float:
+    """Whole-job throughput: the systems all ranks solved per second of the slowest rank's step."""
+    return ws * batch / (ms_step / 1000.0)
 
 
 # --------------------------------------------------------------------- GPU arm
@@ -260,23 +279,13 @@ def run_gpu(args):
                  "iters_mean": statistics.mean(i["iters"] for i in oinf),
                  "max_resid_Lrho": max(i["resid_Lrho"] for i in oinf)}
     infos.clear()
-    ms_step = total_ms / args.steps
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = ws * BATCH / (ms_step / 1000.0)
+    ms_step = _max_over_ranks(total_ms / args.steps, "cuda")
+    value = _job_value(ws, BATCH, ms_step)
 
     # end to end through the same call with host buffers
     infos.clear()
     e2e_times = timed(max(1, min(args.steps, 3)), host=True)
-    e2e_ms = sum(e2e_times) / len(e2e_times)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = _max_over_ranks(sum(e2e_times) / len(e2e_times), "cuda")
     h2d = sum(hv.rp.nbytes + hv.col.nbytes + hv.val.nbytes + sum(c.rp.nbytes + c.col.nbytes + c.val.nbytes
                                                                   for c in cs) for hv, cs in host_inputs)
     d2h = BATCH * d * d * 16
@@ -339,7 +348,7 @@ def run_gpu(args):
                    "tol": TOL,
                    "batch_per_gpu": BATCH, "parallelism": f"replicas x{ws}",
                    "l2": "flushed between timed steps (256 MiB write, outside the events)"},
-        "e2e": {"value": ws * BATCH / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": _job_value(ws, BATCH, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": roofline,
         "clocks": clk.summary(),
