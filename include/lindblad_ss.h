@@ -251,6 +251,42 @@ ss_status krylov_solve(ss_ctx ctx, ss_mat A, ss_prec M, int krylov, const double
 ss_status lgmres_solve(ss_ctx ctx, ss_mat A, ss_prec M, const double* b, double* x, double tol, int maxiter,
                        int restart, int augment, int* iters_out, double* resid_out);
 
+/* ------------------------------------------------ host-side analysis */
+
+/* The host steps of the path, callable without a GPU or a context (the same
+ * code rcm_permute, ilu_factor and the level analysis of the triangular
+ * solves run).  All arrays are host memory owned by the caller; the input is
+ * an n x n CSR pattern with row_ptr[0] = 0, non-decreasing row pointers and
+ * strictly ascending columns in [0, n) in every row, else SS_ERR_INVALID.
+ *
+ * ss_rcm_order_host: reverse Cuthill-McKee order of the pattern of A + A^T
+ * (section "Direct factorization"; start node: the highest-index unvisited
+ * node of minimum degree; neighbours in ascending (degree, index); one pass
+ * per connected component; the sequence reversed).  perm_out[new] = old, n
+ * entries. */
+ss_status ss_rcm_order_host(int64_t n, const int32_t* row_ptr, const int32_t* col, int32_t* perm_out);
+
+/* Level sets of the strict lower (lower != 0) or strict upper triangle:
+ * level(i) = 1 + the largest level of the rows row i depends on (0 without
+ * dependencies).  order_out (n entries) lists the rows by (level, row);
+ * level_ptr_out (n + 1 entries available; *n_levels_out + 1 written) gives
+ * the start of each level in order_out. */
+ss_status ss_level_sets_host(int64_t n, const int32_t* row_ptr, const int32_t* col, int lower,
+                             int32_t* order_out, int32_t* level_ptr_out, int32_t* n_levels_out);
+
+/* ILUT(drop_tol, fill_factor) without pivoting (section "Iterative
+ * solvers"; the rules of ilu_factor with SS_PRECOND_ILUT) on a complex CSR
+ * matrix (val: 2 * nnz doubles, interleaved).  Output: the combined factors
+ * (strict lower part = L with unit diagonal, diagonal and upper part = U),
+ * ascending columns.  *nnz_out receives their entry count; when it exceeds
+ * `capacity` nothing else is written and SS_ERR_INVALID is returned (call
+ * again with enough room: f_row_ptr n + 1, f_col nnz, f_val 2 nnz entries).
+ * SS_ZERO_PIVOT with *zero_pivot_row = the row of a zero or missing pivot
+ * (else -1). */
+ss_status ss_ilut_host(int64_t n, const int32_t* row_ptr, const int32_t* col, const double* val, double drop_tol,
+                       double fill_factor, int64_t capacity, int32_t* f_row_ptr, int32_t* f_col, double* f_val,
+                       int64_t* nnz_out, int64_t* zero_pivot_row);
+
 /* Largest system krylov_solve_noalloc accepts (complex unknowns). */
 #define SS_NOALLOC_MAX_N 65536
 

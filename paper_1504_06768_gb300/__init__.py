@@ -97,6 +97,56 @@ class _CsrHost:
                               self.val.ctypes.data, 0)
 
 
+def _host_status(st: int, what: str):
+    if st != B.SS_OK:
+        raise SolverError(st, f"{what}: {B.STATUS_NAMES.get(st, st)}")
+
+
+def rcm_order_host(A):
+    """Reverse Cuthill-McKee order of the pattern of A + A^T computed on the
+    host (no GPU): perm[new] = old."""
+    h = _CsrHost(A)
+    n = h.view.n_rows
+    perm = np.empty(n, dtype=np.int32)
+    _host_status(B.load().ss_rcm_order_host(n, h.rp.ctypes.data, h.col.ctypes.data, perm.ctypes.data),
+                 "ss_rcm_order_host")
+    return perm
+
+
+def level_sets_host(A, lower: bool = True):
+    """Level sets of the strict lower (or upper) triangle of A's pattern on
+    the host: (order, level_ptr)."""
+    h = _CsrHost(A)
+    n = h.view.n_rows
+    order = np.empty(n, dtype=np.int32)
+    ptr = np.empty(n + 1, dtype=np.int32)
+    nl = C.c_int32()
+    _host_status(B.load().ss_level_sets_host(n, h.rp.ctypes.data, h.col.ctypes.data, int(lower), order.ctypes.data,
+                                             ptr.ctypes.data, C.byref(nl)), "ss_level_sets_host")
+    return order, ptr[:nl.value + 1].copy()
+
+
+def ilut_host(A, drop_tol: float = 1e-4, fill_factor: float = 10.0):
+    """ILUT factors of A computed on the host (no GPU), as a scipy CSR matrix
+    of the combined factors (strict lower = L with unit diagonal, rest = U)."""
+    import scipy.sparse as sp
+    h = _CsrHost(A)
+    n = h.view.n_rows
+    lib = B.load()
+    nnz, bad = C.c_int64(), C.c_int64()
+    st = lib.ss_ilut_host(n, h.rp.ctypes.data, h.col.ctypes.data, h.val.ctypes.data, drop_tol, fill_factor, 0,
+                          None, None, None, C.byref(nnz), C.byref(bad))
+    if st == B.SS_ZERO_PIVOT:
+        raise SolverError(st, f"ss_ilut_host: zero pivot in row {bad.value}")
+    rp = np.empty(n + 1, dtype=np.int32)
+    col = np.empty(max(nnz.value, 1), dtype=np.int32)
+    val = np.empty(max(nnz.value, 1), dtype=np.complex128)
+    _host_status(lib.ss_ilut_host(n, h.rp.ctypes.data, h.col.ctypes.data, h.val.ctypes.data, drop_tol, fill_factor,
+                                  nnz.value, rp.ctypes.data, col.ctypes.data, val.ctypes.data, C.byref(nnz),
+                                  C.byref(bad)), "ss_ilut_host")
+    return sp.csr_matrix((val[:nnz.value], col[:nnz.value], rp), shape=(n, n))
+
+
 class Matrix:
     """A library-owned complex FP64 CSR matrix on the device."""
 
