@@ -287,6 +287,20 @@ ss_status ss_ilut_host(int64_t n, const int32_t* row_ptr, const int32_t* col, co
                        double fill_factor, int64_t capacity, int32_t* f_row_ptr, int32_t* f_col, double* f_val,
                        int64_t* nnz_out, int64_t* zero_pivot_row);
 
+/* Weighted maximum bipartite matching (section "Direct factorization"): a
+ * row permutation that makes the diagonal zero-free when A is structurally
+ * nonsingular, trying to put large entries on it.  Columns are taken in
+ * descending order of their largest |a_ij|^2 (ties: ascending column); each
+ * runs a breadth-first search over alternating paths that tries the rows of
+ * a column in descending |a_ij|^2 (ties: ascending row) and flips the path to
+ * the first unmatched row.  match_out[j] (n entries) = the row assigned to
+ * column j, or -1 when column j has no augmenting path; *matched_out = the
+ * number of matched columns (n: A[match_out, :] has a zero-free diagonal).
+ * val: 2 * nnz doubles, interleaved.  The device path does not apply it: the
+ * trace-row Liouvillians of the workloads have a full diagonal. */
+ss_status ss_mbm_host(int64_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
+                      int32_t* match_out, int64_t* matched_out);
+
 /* Largest system krylov_solve_noalloc accepts (complex unknowns). */
 #define SS_NOALLOC_MAX_N 65536
 

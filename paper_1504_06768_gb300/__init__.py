@@ -113,6 +113,19 @@ def rcm_order_host(A):
     return perm
 
 
+def mbm_host(A):
+    """Weighted maximum bipartite matching on the host (no GPU): (match,
+    matched) with match[j] = the row assigned to column j (-1 if none), so
+    that A[match, :] has a zero-free diagonal when matched == n."""
+    h = _CsrHost(A)
+    n = h.view.n_rows
+    match = np.empty(n, dtype=np.int32)
+    matched = C.c_int64()
+    _host_status(B.load().ss_mbm_host(n, h.rp.ctypes.data, h.col.ctypes.data, h.val.ctypes.data, match.ctypes.data,
+                                      C.byref(matched)), "ss_mbm_host")
+    return match, matched.value
+
+
 def level_sets_host(A, lower: bool = True):
     """Level sets of the strict lower (or upper) triangle of A's pattern on
     the host: (order, level_ptr)."""

@@ -102,6 +102,7 @@ _SIGNATURES = {
     "ss_level_sets_host": (C.c_int, [C.c_int64, _P, _P, C.c_int, _P, _P, C.POINTER(C.c_int32)]),
     "ss_ilut_host": (C.c_int, [C.c_int64, _P, _P, _P, C.c_double, C.c_double, C.c_int64, _P, _P, _P,
                                _I64P, _I64P]),
+    "ss_mbm_host": (C.c_int, [C.c_int64, _P, _P, _P, _P, _I64P]),
     "krylov_solve_noalloc": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int, C.POINTER(C.c_int), _DP]),
     "steady_state": (C.c_int, [_P, C.POINTER(CsrView), C.c_int, C.POINTER(CsrView), C.POINTER(Options),
                                _P, C.c_int, C.POINTER(Info)]),

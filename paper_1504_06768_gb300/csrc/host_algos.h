@@ -33,3 +33,12 @@ void level_units_host(const std::vector<int32_t>& order, const std::vector<int32
 int64_t ilut_host(int64_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
                   double drop_tol, double fill_factor, std::vector<int32_t>& f_row_ptr,
                   std::vector<int32_t>& f_col, std::vector<double>& f_val);
+
+// Weighted maximum bipartite matching (section "Direct factorization"):
+// match[j] = the row assigned to column j (-1 if none), so that A[match, :]
+// has a zero-free diagonal when A is structurally nonsingular.  Columns go in
+// descending order of their largest |a_ij|^2 (ties: ascending column); each
+// runs a breadth-first augmenting-path search trying rows in descending
+// |a_ij|^2 (ties: ascending row).  val: interleaved complex.  Returns the
+// number of matched columns (n when the diagonal can be made zero-free).
+int64_t mbm_host(int64_t n, const int32_t* row_ptr, const int32_t* col, const double* val, int32_t* match);

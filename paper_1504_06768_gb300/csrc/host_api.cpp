@@ -1,6 +1,7 @@
 // Host-side steps of the path as C entry points that need no GPU: the RCM
-// ordering of rcm_permute, the level sets of the triangular solves and the
-// ILUT of ilu_factor (the same functions the device path calls).
+// ordering of rcm_permute, the level sets of the triangular solves, the ILUT
+// of ilu_factor (the same functions the device path calls) and the weighted
+// bipartite matching for a zero-free diagonal.
 #include <cstring>
 #include <vector>
 
@@ -61,5 +62,13 @@ extern "C" ss_status ss_ilut_host(int64_t n, const int32_t* row_ptr, const int32
         std::memcpy(f_col, fcol.data(), sizeof(int32_t) * (size_t)nnz);
         std::memcpy(f_val, fval.data(), sizeof(double) * 2 * (size_t)nnz);
     }
+    return SS_OK;
+}
+
+extern "C" ss_status ss_mbm_host(int64_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
+                                 int32_t* match_out, int64_t* matched_out) {
+    if (!match_out || !matched_out || !csr_ok(n, row_ptr, col) || (n > 0 && row_ptr[n] > 0 && !val))
+        return SS_ERR_INVALID;
+    *matched_out = mbm_host(n, row_ptr, col, val, match_out);
     return SS_OK;
 }

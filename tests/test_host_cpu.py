@@ -122,3 +122,34 @@ def test_host_entry_points_reject_malformed_csr(ss):
     ptr = np.empty(3, dtype=np.int32)
     assert B.load().ss_level_sets_host(2, rp.ctypes.data, col.ctypes.data, 1, order.ctypes.data, ptr.ctypes.data,
                                        C.byref(nl)) == B.SS_ERR_INVALID
+
+
+# ---------------------------------------------------------- bipartite matching
+
+def _random_complex(n, density, seed):
+    rng = np.random.default_rng(seed)
+    A = sp.random(n, n, density=density, random_state=rng, format="csr")
+    A.data = A.data + 1j * rng.random(A.nnz)
+    A.data[rng.random(A.nnz) < 0.2] = 1.0                          # ties of equal weight
+    A.sort_indices()
+    return A
+
+
+@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("density", [0.03, 0.1])
+def test_mbm_host_is_the_oracles_matching(ss, seed, density):
+    from oracle.matching import weighted_mbm
+    A = _random_complex(80, density, seed)
+    match, k = ss.mbm_host(A)
+    ref, kr = weighted_mbm(A)
+    assert k == kr and np.array_equal(match, ref)
+
+
+@pytest.mark.parametrize("name", sorted(SYSTEMS))
+def test_mbm_host_on_trace_row_liouvillians(ss, name):
+    from oracle.matching import weighted_mbm
+    A = _modified(SYSTEMS[name]())
+    match, k = ss.mbm_host(A)
+    ref, kr = weighted_mbm(A)
+    assert k == kr == A.shape[0] and np.array_equal(match, ref)
+    assert np.all(A[match, :].diagonal() != 0)
