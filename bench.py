@@ -136,6 +136,16 @@ def _max_over_ranks(x: float, device) -> float:
     return float(t.item())
 
 
+def _trace_distances(a, b, d: int):
+    """Trace distance between corresponding column-major d x d density
+    matrices (rows of a and b): 1/2 sum |eig(h)|, h the Hermitian part of the
+    difference."""
+    import numpy as np
+    x = (a - b).reshape(-1, d, d).transpose(0, 2, 1)     # column-major storage -> matrices
+    h = 0.5 * (x + x.conj().transpose(0, 2, 1))
+    return 0.5 * np.abs(np.linalg.eigvalsh(h)).sum(axis=1)
+
+
 def _job_value(ws: int, batch: int, ms_step: float) -> float:
     """Whole-job throughput: the systems all ranks solved per second of the slowest rank's step."""
     return ws * batch / (ms_step / 1000.0)
@@ -263,6 +273,7 @@ def run_gpu(args):
         prof[name] = (cnt.value, ms.value)
     step_infos = list(infos)
     total_ms = sum(times)
+    rho_main = rho_dev.cpu().numpy()                 # the last timed step's results
     # the same step in the other precision, for the mixed-versus-FP64 comparison
     other = None
     if not args.no_compare:
@@ -275,10 +286,15 @@ def run_gpu(args):
         oinf = list(infos)
         opt.precision = saved
         oms = sum(ot) / len(ot)
+        td = _trace_distances(rho_main, rho_dev.cpu().numpy(), d)
         other = {"precision": "fp64" if args.precision == "mixed" else "mixed",
                  "value": BATCH / (oms / 1000.0), "ms_per_step": oms,
                  "iters_mean": statistics.mean(i["iters"] for i in oinf),
-                 "max_resid_Lrho": max(i["resid_Lrho"] for i in oinf)}
+                 "max_resid_Lrho": max(i["resid_Lrho"] for i in oinf),
+                 "trace_distance_to_headline": {
+                     "max": float(td.max()), "median": float(np.median(td)), "systems": int(td.size),
+                     "what": "per system, T(rho_mixed, rho_fp64) = 1/2 sum |eig(Hermitian part of the "
+                             "difference)|, the same seeds solved by both paths"}}
     infos.clear()
     ms_step = _max_over_ranks(total_ms / args.steps, "cuda")
     value = _job_value(ws, BATCH, ms_step)
@@ -524,6 +540,18 @@ def _oracle_solve_one(seed: int, dense: bool = False, cavity: int = JC_N) -> flo
 
 
 _ORACLE_POOL_FAILED = [False]
+_WORKER_BARRIER = [None]
+
+
+def _oracle_worker_init(barrier, dense: bool) -> None:
+    """Pool initializer: imports and one small solve (cavity 4), so that no
+    worker pays its start-up inside the timed region."""
+    _WORKER_BARRIER[0] = barrier
+    _oracle_solve_one(0, dense, 4)
+
+
+def _oracle_worker_sync(_k: int) -> None:
+    _WORKER_BARRIER[0].wait(timeout=120)
 
 
 def _oracle_workers() -> int:
@@ -541,9 +569,13 @@ def _oracle_solves(count: int, start_seed: int = 0, dense: bool = False) -> floa
     for k in saved:
         os.environ[k] = "1"                       # one BLAS thread per worker: `workers` cores in all
     try:
-        with mp.get_context("spawn").Pool(workers) as pool:
-            # imports and warm-up; a worker lost on the way would leave a plain wait hanging
-            pool.starmap_async(_oracle_solve_one, [(k, dense, 4) for k in range(workers)]).get(timeout=120)
+        mpc = mp.get_context("spawn")
+        barrier = mpc.Barrier(workers)
+        with mpc.Pool(workers, initializer=_oracle_worker_init, initargs=(barrier, dense)) as pool:
+            # every worker warm before t0: each of `workers` tasks waits at the barrier until
+            # all are taken, so each worker takes exactly one after its initializer has run (a
+            # worker lost on the way breaks the barrier instead of leaving the wait hanging)
+            pool.map_async(_oracle_worker_sync, range(workers), chunksize=1).get(timeout=180)
             t0 = time.perf_counter()
             pool.starmap_async(_oracle_solve_one, [(start_seed + k, dense) for k in range(count)],
                                chunksize=1).get(timeout=300)

@@ -312,12 +312,18 @@ ss_status ss_mbm_host(int64_t n, const int32_t* row_ptr, const int32_t* col, con
  * Krylov vectors of up to SS_NOALLOC_MAX_N = 65,536 complex doubles, the
  * solver state and the reduction partials, about 8.3 MiB) is a fixed array in
  * the library's device memory that every GPU loading the library holds until
- * the process exits.  The array's device address is looked up once per device
- * by the first call on that device (make that first call before any stream
- * capture).  Every call shares the array and overwrites what the previous
- * call left there; calls whose work overlaps on the same GPU race and must
- * not be issued concurrently.  Arguments as for krylov_solve; b and x are
- * device arrays of 2n doubles, x holds the initial guess.
+ * the process exits.  ss_ctx_create loads that array onto its device and
+ * looks up its address (so with CUDA's lazy module loading the array comes
+ * into existence there, and ss_ctx_create returns SS_ERR_OOM / SS_ERR_CUDA if
+ * it cannot); no call of this function allocates it.  Every call shares the
+ * array and overwrites what the previous call left there, and the host-side
+ * mirror of the solver state is shared per device as well: calls on the same
+ * GPU whose work could overlap (other streams, other host threads) race and
+ * must be serialised by the caller.  The call synchronises the context's
+ * stream (it reads the solver state back between chunks of iterations), so
+ * it must not be issued on a stream that is being captured.  Arguments as
+ * for krylov_solve; b and x are device arrays of 2n doubles, x holds the
+ * initial guess.
  * Errors: SS_ERR_INVALID when n > SS_NOALLOC_MAX_N (use krylov_solve), plus
  * the statuses of krylov_solve.  The paper has no counterpart of this entry
  * point; it is an interface variant of the BiCGSTAB solve. */
@@ -411,6 +417,10 @@ ss_status ss_profile_read(ss_ctx ctx, int kind, int64_t* launches, double* total
 /* Number of CUDA kernels this library has launched in the process so far
  * (all contexts). */
 unsigned long long ss_launch_count(void);
+/* Number of device and pinned-host memory allocations this library has made
+ * in the process so far (all contexts): a call that allocates nothing leaves
+ * it unchanged. */
+unsigned long long ss_alloc_count(void);
 
 #ifdef __cplusplus
 }

@@ -96,6 +96,7 @@ _SIGNATURES = {
     "ss_profile_enable": (C.c_int, [_P, C.c_int]),
     "ss_profile_read": (C.c_int, [_P, C.c_int, _I64P, _DP]),
     "ss_launch_count": (C.c_ulonglong, []),
+    "ss_alloc_count": (C.c_ulonglong, []),
     "lgmres_solve": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int, C.c_int, C.c_int,
                                C.POINTER(C.c_int), _DP]),
     "ss_rcm_order_host": (C.c_int, [C.c_int64, _P, _P, _P]),

@@ -124,6 +124,12 @@ ss_status cuda_check(ss_ctx ctx, cudaError_t e, const char* what);
 // Every kernel launch of the library goes through ss_count_launch() (in the
 // grid expression of the launch), so the total is available to callers.
 int ss_count_launch();
+// Every device or pinned-host allocation the library makes is counted
+// (ss_alloc_count), so a caller can check that a call allocated nothing.
+void ss_count_alloc();
+// Loads the allocation-free entry point's fixed workspace onto the context's
+// device and records its address (once per device); called by ss_ctx_create.
+ss_status noalloc_prepare(ss_ctx ctx);
 
 // RAII event pair around one launch when the context's profiler is on.
 struct ProfScope {

@@ -445,6 +445,7 @@ ss_status krylov_workspace(ss_ctx ctx, KrylovWork& w, int64_t n, int method, int
     size_t nvec = method == SS_KRYLOV_GMRES ? (size_t)(2 * (m + kaug) + 1 + (kaug > 0 ? 1 : 0)) : 8;
     SS_TRY(dev_alloc_n(ctx, &w.vecs, nvec * (size_t)n));
     w.nvec = nvec;
+    ss_count_alloc();
     SS_CUDA(ctx, cudaHostAlloc(reinterpret_cast<void**>(&w.host_st), sizeof(KrylovState), cudaHostAllocDefault));
     return SS_OK;
 }

@@ -6,11 +6,16 @@
 // The Krylov workspace (eight vectors of at most SS_NOALLOC_MAX_N complex
 // doubles, the device-side solver state and the reduction partials) lives in
 // one file-scope __device__ array.  Every GPU that loads the library holds
-// that array until the process exits.  The array is shared by all calls on a
-// device and keeps the last call's contents; the solver initialises every
-// word it reads, so nothing from an earlier call leaks into a result.  Two
-// calls whose work overlaps on the same GPU (different streams or host
-// threads) race on the array.
+// that array until the process exits.  With lazy module loading (the CUDA
+// default) the array only comes into existence when its module is first
+// touched, so ss_ctx_create touches it (noalloc_prepare): the call that
+// creates a context loads the array and looks up its device address, and no
+// krylov_solve_noalloc call ever allocates.  The array is shared by all calls
+// on a device and keeps the last call's contents; the solver initialises
+// every word it reads, so nothing from an earlier call leaks into a result.
+// Two calls whose work overlaps on the same GPU (different streams or host
+// threads) race on the array, and on the per-device host mirror of the
+// solver state as well.
 #include <mutex>
 
 #include "common.cuh"
@@ -49,6 +54,11 @@ ss_status scratch_for(ss_ctx ctx, void** out) {
 }
 
 }  // namespace
+
+ss_status noalloc_prepare(ss_ctx ctx) {
+    void* p = nullptr;
+    return scratch_for(ctx, &p);
+}
 
 extern "C" ss_status krylov_solve_noalloc(ss_ctx ctx, ss_mat A, ss_prec M, const double* b, double* x, double tol,
                                           int maxiter, int* iters_out, double* resid_out) {

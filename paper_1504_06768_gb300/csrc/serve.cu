@@ -179,6 +179,7 @@ void fast_lane(ss_server s) {
             if (sl.pinned) cudaFreeHost(sl.pinned);
             sl.pinned = nullptr;
             sl.pinned_bytes = 0;
+            ss_count_alloc();
             if (cudaMallocHost(reinterpret_cast<void**>(&sl.pinned), grow) != cudaSuccess) {
                 cudaGetLastError();
                 st = SS_ERR_OOM;

@@ -20,6 +20,7 @@ ss_status cuda_check(ss_ctx ctx, cudaError_t e, const char* what) {
 // reused by later calls on the same stream without a device synchronisation.
 ss_status dev_alloc(ss_ctx ctx, void** p, size_t bytes) {
     *p = nullptr;
+    ss_count_alloc();
     cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -270,3 +271,11 @@ int ss_count_launch() {
 }
 
 extern "C" unsigned long long ss_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+// ------------------------------------------------------- allocation count
+
+static std::atomic<unsigned long long> g_allocs{0};
+
+void ss_count_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" unsigned long long ss_alloc_count(void) { return g_allocs.load(std::memory_order_relaxed); }

@@ -51,11 +51,17 @@ def test_noalloc_matches_krylov_solve_twice(ss):
         for call in range(2):                        # the second call reuses the dirty shared array
             x = torch.zeros(n, dtype=torch.complex128, device="cuda")
             it, res = ctypes.c_int(), ctypes.c_double()
+            torch.cuda.synchronize()
+            allocs0, free0 = lib.ss_alloc_count(), torch.cuda.mem_get_info()[0]
             st = lib.krylov_solve_noalloc(Ap.ctx.handle, Ap.handle, M.handle, ctypes.c_void_p(bd.data_ptr()),
                                           ctypes.c_void_p(x.data_ptr()), 1e-12 * w, 1000, ctypes.byref(it),
                                           ctypes.byref(res))
             torch.cuda.synchronize()
             assert st == 0, lib.ss_last_error(Ap.ctx.handle).decode()
+            # nothing was allocated: not by the library (its allocation counter),
+            # and no new device memory was taken by anyone in the call
+            assert lib.ss_alloc_count() == allocs0, call
+            assert torch.cuda.mem_get_info()[0] == free0, call
             assert res.value <= 1e-12 * w and it.value == it_ref
             err = (x - ref).abs().max().item()
             assert err <= 1e-10 * ref.abs().max().item(), (call, err)
