@@ -381,6 +381,10 @@ def run_gpu(args):
         out["spmv"] = spmv_measure(ss, B, ctx, stream)
     if rank == 0 and not args.no_serve:
         out["serving"] = serve_measure(ss, args)
+    if rank == 0 and not args.no_configs:
+        out["configs"] = configs_measure(ss)
+    if rank == 0 and not args.no_serve:
+        out["serving_sweep"] = serve_sweep(ss, args)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     if ws > 1:
@@ -402,6 +406,7 @@ def _time_spmv(ss, B, ctx, stream, Ap, reps):
     stream.  Bytes: the CSR once (values + int32 columns + row pointers) and
     x, y once each."""
     import ctypes as C
+    import numpy as np
     import torch
     n, nnz = Ap.shape[0], Ap.nnz
     lib = B.load()
@@ -411,6 +416,11 @@ def _time_spmv(ss, B, ctx, stream, Ap, reps):
     y32 = torch.empty_like(x32)
     peak, kind = _peaks()
     res = {"n": n, "nnz": nnz}
+    # the FP64 SpMV runs on the part-split copy of A (one real value and a
+    # column word per nonzero real or imaginary part): its own bytes and FMAs
+    As = Ap.to_scipy()
+    parts = int(np.count_nonzero(As.data.real) + np.count_nonzero(As.data.imag))
+    del As
     for name, fn, vb in (("fp64", lambda: lib.spmv(ctx.handle, Ap.handle, C.c_void_p(x.data_ptr()),
                                                     C.c_void_p(y.data_ptr())), 16),
                          ("fp32", lambda: lib.spmv_f32(ctx.handle, Ap.handle, C.c_void_p(x32.data_ptr()),
@@ -429,9 +439,14 @@ def _time_spmv(ss, B, ctx, stream, Ap, reps):
         gbs = bytes_ / (ms / 1000.0) / 1e9
         res[name] = {"us": 1000.0 * ms, "bytes": bytes_, "GB/s": gbs, "frac_hbm": gbs / peak,
                      "peak_source": kind}
-    # FP64 complex SpMV does 4 DFMA per stored entry; GB300 runs FP64 FMA at
-    # about 1.26 TFLOP/s (measured), so that form is bound by the FP64 pipe
-    res["fp64"]["fp64_tflops"] = 8.0 * nnz / (res["fp64"]["us"] * 1e-6) / 1e12
+    # complex CSR bytes above (20 nnz + 36 n); the split form moves 12 bytes
+    # per part and does 2 FP64 FMAs per part (GB300: about 1.26 TFLOP/s FP64)
+    sb = parts * 12 + (n + 1) * 4 + 2 * n * 16
+    us = res["fp64"]["us"]
+    res["fp64"].update({"format": "part-split (value + column word per nonzero real/imaginary part)",
+                        "parts": parts, "bytes_split": sb, "GB/s_split": sb / (us * 1e-6) / 1e9,
+                        "frac_hbm_split": sb / (us * 1e-6) / 1e9 / peak,
+                        "fp64_tflops": 4.0 * parts / (us * 1e-6) / 1e12})
     return res, x, x32
 
 
@@ -470,7 +485,10 @@ def spmv_measure(ss, B, ctx, stream, reps: int = 20):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / 5
-        bytes_ = nnz * (vb + 4) + (n + 1) * 4 * 2 + n * (4 * vb + 3 * 4)
+        # each strict triangle once (value + column), per row its record (row
+        # id, entry offset: 8 B), b read, x written, the other solve's vector
+        # re-marked, and for the upper triangle 1 / u_ii
+        bytes_ = (nnz - n) * (vb + 4) + n * (16 + 7 * vb)
         gbs = bytes_ / (ms / 1000.0) / 1e9
         trsv[name] = {"us": 1000.0 * ms, "bytes": bytes_, "GB/s": gbs, "frac_hbm": gbs / peak}
     trsv["levels"] = [M.info()["levels_lower"], M.info()["levels_upper"]]
@@ -520,34 +538,211 @@ def serve_measure(ss, args):
             "waves": stats["waves"], "precision": args.precision}
 
 
+def _td_list(rhos_a, rhos_b):
+    """Trace distances between corresponding d x d density matrices."""
+    import numpy as np
+    out = []
+    for a, b in zip(rhos_a, rhos_b):
+        x = a - b
+        out.append(0.5 * float(np.abs(np.linalg.eigvalsh(0.5 * (x + x.conj().T))).sum()))
+    return np.array(out)
+
+
+def _td_stats(td):
+    import numpy as np
+    return {"max": float(np.max(td)), "median": float(np.median(td))} if len(td) else None
+
+
+def configs_measure(ss):
+    """The other configurations of the workload list, each through the public
+    API with host inputs (wall time around complete calls):
+    * 512 driven Kerr oscillators (seed 0; cutoffs N ~ U{8..64}, n = 64..4096)
+      in one steady_state_batched call, mixed and FP64, against the same 512
+      solved one at a time by steady_state in FP64 (the plain GPU path);
+    * optomechanics 10 x 40 (n = 160,000) by steady_state, mixed and FP64;
+    * JC40 with ILUT(1e-4, 10) by BiCGSTAB and by GMRES(30) (FP64)."""
+    import numpy as np
+    from workloads import jaynes_cummings_rwa, kerr_sweep, optomechanics
+    res = {}
+    kerr = kerr_sweep(512, seed=0)
+    pairs = [(s.H, s.c_ops) for s in kerr]
+    k4 = {"systems": len(kerr), "n_range": [min(s.d for s in kerr) ** 2, max(s.d for s in kerr) ** 2],
+          "tol": TOL}
+    rb = {}
+    for prec in ("mixed", "fp64"):
+        ss.steady_state_batched(pairs[:8], tol=TOL, precision=prec)          # warm
+        times = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            rhos, infos = ss.steady_state_batched(pairs, tol=TOL, precision=prec, raise_on_failure=False)
+            times.append(time.perf_counter() - t0)
+        rb[prec] = rhos
+        k4[f"batched_{prec}"] = {"solves_per_s": len(kerr) / statistics.median(times),
+                                 "s_per_call": statistics.median(times),
+                                 "converged": sum(i["status"] == 0 and i["resid_Lrho"] <= TOL for i in infos),
+                                 "iters_mean": statistics.mean(i["iters"] for i in infos)}
+    t0 = time.perf_counter()
+    single, sinfo = [], []
+    for H, cs in pairs:
+        rho, info = ss.steady_state(H, cs, tol=TOL, precision="fp64", raise_on_failure=False)
+        single.append(rho)
+        sinfo.append(info)
+    dt = time.perf_counter() - t0
+    k4["one_at_a_time_fp64"] = {"solves_per_s": len(kerr) / dt, "s_total": dt,
+                                "converged": sum(i["status"] == 0 and i["resid_Lrho"] <= TOL for i in sinfo),
+                                "iters_mean": statistics.mean(i["iters"] for i in sinfo)}
+    k4["speedup_batched_mixed_vs_one_at_a_time_fp64"] = (k4["batched_mixed"]["solves_per_s"]
+                                                         / k4["one_at_a_time_fp64"]["solves_per_s"])
+    k4["trace_distance_batched_mixed_vs_one_at_a_time_fp64"] = _td_stats(_td_list(rb["mixed"], single))
+    k4["trace_distance_batched_fp64_vs_one_at_a_time_fp64"] = _td_stats(_td_list(rb["fp64"], single))
+    res["kerr512"] = k4
+
+    opto = [optomechanics(seed=s) for s in range(2)]
+    c3 = {"systems": len(opto), "n": opto[0].d ** 2, "tol": TOL}
+    ro = {}
+    for prec in ("mixed", "fp64"):
+        t0 = time.perf_counter()
+        out = [ss.steady_state(s.H, s.c_ops, tol=TOL, precision=prec, raise_on_failure=False) for s in opto]
+        dt = time.perf_counter() - t0
+        ro[prec] = [o[0] for o in out]
+        c3[prec] = {"solves_per_s": len(opto) / dt, "s_per_solve": dt / len(opto),
+                    "iters": [o[1]["iters"] for o in out], "resid_Lrho": [o[1]["resid_Lrho"] for o in out],
+                    "converged": sum(o[1]["status"] == 0 for o in out)}
+    c3["trace_distance_mixed_vs_fp64"] = _td_stats(_td_list(ro["mixed"], ro["fp64"]))
+    res["optomechanics"] = c3
+
+    jc = [jaynes_cummings_rwa(seed=s) for s in range(4)]
+    c2 = {"systems": len(jc), "n": 6400, "precond": "ilut(1e-4, 10)", "tol": TOL}
+    for meth in ("iterative-bicgstab", "iterative-lgmres"):
+        t0 = time.perf_counter()
+        out = [ss.steady_state(s.H, s.c_ops, method=meth, precond="ilut", tol=TOL, restart=30,
+                               raise_on_failure=False) for s in jc]
+        dt = time.perf_counter() - t0
+        c2["bicgstab" if "bicg" in meth else "gmres30"] = {
+            "solves_per_s": len(jc) / dt, "iters": [o[1]["iters"] for o in out],
+            "converged": sum(o[1]["status"] == 0 for o in out), "nnz_factors": out[0][1]["nnz_factors"],
+            "max_resid_Lrho": max(o[1]["resid_Lrho"] for o in out)}
+    res["jc40_ilut"] = c2
+    return res
+
+
+def serve_sweep(ss, args):
+    """Poisson arrival streams (seeded) at rates 10..1000 requests/s through
+    the serving loop, mixed and FP64.  The mix: JC40 (config 2), Kerr
+    oscillators with cutoffs 8..64 (config 4) and, one request in 150, the
+    optomechanical system (config 3, n = 160,000, outside the persistent
+    kernel's size range: served by the single-system lane).  Each rate runs
+    about 3 s of arrivals (at least 30 requests)."""
+    import numpy as np
+    from workloads import jaynes_cummings_rwa, kerr_sweep, optomechanics
+    pool_jc = [jaynes_cummings_rwa(seed=2000 + k, N=JC_N) for k in range(24)]
+    pool_kerr = kerr_sweep(64, seed=11)
+    opto = optomechanics(seed=3)
+    out = {"mix": "JC40 (n=6400) 1/2, Kerr N~U{8..64} 1/2, optomechanics 10x40 (n=160,000) 1 in 150",
+           "rates": [10, 30, 100, 300, 1000], "runs": []}
+    for prec in ("mixed", "fp64"):
+        with ss.Server(precision=prec, tol=TOL) as srv:
+            for sysm in (pool_jc[0], pool_kerr[0], opto):       # warm each pattern class
+                srv.wait(srv.submit(sysm.H, sysm.c_ops), timeout_s=600, raise_on_failure=False)
+            for rate in out["rates"]:
+                rng = np.random.default_rng(rate)
+                n_req = max(30, int(3.0 * rate))
+                gaps = rng.exponential(1.0 / rate, size=n_req)
+                kinds = rng.random(n_req)
+                picks = rng.integers(0, 1 << 30, size=n_req)
+                t0 = time.perf_counter()
+                due = t0
+                tickets = []
+                for k in range(n_req):
+                    due += gaps[k]
+                    delay = due - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                    if k % 150 == 75:
+                        sysm, cls = opto, "opto"
+                    elif kinds[k] < 0.5:
+                        sysm, cls = pool_jc[picks[k] % len(pool_jc)], "jc40"
+                    else:
+                        sysm, cls = pool_kerr[picks[k] % len(pool_kerr)], "kerr"
+                    tickets.append((srv.submit(sysm.H, sysm.c_ops), cls))
+                lat, ok, by = [], 0, {}
+                for t, cls in tickets:
+                    _, info, ms = srv.wait(t, timeout_s=600, raise_on_failure=False)
+                    lat.append(ms)
+                    good = info["status"] == 0 and info["resid_Lrho"] <= TOL
+                    ok += good
+                    by.setdefault(cls, []).append(ms)
+                wall = time.perf_counter() - t0
+                lat = np.array(lat)
+                out["runs"].append({"precision": prec, "rate_per_s": rate, "requests": n_req,
+                                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                                    "solves_per_s": n_req / wall, "converged": int(ok),
+                                    "p50_ms_by_class": {c: float(np.percentile(v, 50)) for c, v in by.items()}})
+    return out
+
+
 # ----------------------------------------------------------- CPU (oracle) arm
 
-def _oracle_solve_one(seed: int, dense: bool = False, cavity: int = JC_N) -> float:
-    """Seconds the oracle takes for one JC40 system: by default its sparse
-    CPU pipeline (RCM, iLU(0), BiCGSTAB in FP64 to ||L rho|| <= 1e-10, the
-    plain CPU iterative solver of the paper's method); dense=True uses its
-    dense FP64 LU of the trace-row system instead."""
+def _scipy_spilu_solve(H, c_ops) -> bool:
+    """SciPy's incomplete LU (SuperLU ILUTP: drop 1e-4, fill 10) and BiCGSTAB
+    on the RCM-ordered trace-row system (SciPy's own RCM); the system is
+    built by the oracle's sparse Liouvillian.  True when ||L rho|| <= TOL."""
+    import numpy as np
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+    from scipy.sparse.csgraph import reverse_cuthill_mckee
+    from oracle.liouvillian import default_weight, liouvillian_sparse, modified_liouvillian
+    L = sp.csr_matrix(liouvillian_sparse(H, c_ops))
+    d = H.shape[0]
+    w = default_weight(L)
+    A, b = modified_liouvillian(L, d, w)
+    p = reverse_cuthill_mckee((abs(A) + abs(A).T).tocsr(), symmetric_mode=True)
+    Ap = A[p][:, p].tocsc()
+    bp = b[p]
+    try:
+        ilu = sla.spilu(Ap, drop_tol=1e-4, fill_factor=10)
+    except RuntimeError:                 # SuperLU: "Factor is exactly singular" on some systems
+        return False
+    M = sla.LinearOperator(Ap.shape, matvec=ilu.solve, dtype=complex)
+    xp, _ = sla.bicgstab(Ap, bp, M=M, rtol=0.0, atol=0.5 * TOL, maxiter=1000)
+    x = np.empty_like(xp)
+    x[p] = xp
+    rho = x.reshape((d, d), order="F")
+    rho = rho / np.trace(rho)
+    return float(np.linalg.norm(L @ rho.reshape(-1, order="F"))) <= TOL
+
+
+def _oracle_solve_one(seed: int, kind: str = "sparse", cavity: int = JC_N):
+    """Seconds one JC40 system takes on the CPU: kind "sparse" is the
+    oracle's sparse pipeline (RCM, iLU(0), BiCGSTAB in FP64 to
+    ||L rho|| <= 1e-10, the plain CPU iterative solver of the paper's method);
+    "dense" the oracle's dense FP64 LU of the trace-row system; "scipy"
+    SciPy's spilu + BiCGSTAB (_scipy_spilu_solve).  Returns (seconds, reached
+    ||L rho|| <= TOL)."""
     from oracle.krylov import steady_state_iterative
     from oracle.steady import steady_state_dense
     from workloads import jaynes_cummings_rwa
     sysm = jaynes_cummings_rwa(seed=seed, N=cavity)
     t0 = time.perf_counter()
-    if dense:
+    ok = True
+    if kind == "dense":
         steady_state_dense(sysm.H, sysm.c_ops)
+    elif kind == "scipy":
+        ok = _scipy_spilu_solve(sysm.H, sysm.c_ops)
     else:
-        steady_state_iterative(sysm.H, sysm.c_ops, method="bicgstab", precond="ilu0", tol=TOL)
-    return time.perf_counter() - t0
+        ok = steady_state_iterative(sysm.H, sysm.c_ops, method="bicgstab", precond="ilu0", tol=TOL).status == 0
+    return time.perf_counter() - t0, ok
 
 
 _ORACLE_POOL_FAILED = [False]
 _WORKER_BARRIER = [None]
 
 
-def _oracle_worker_init(barrier, dense: bool) -> None:
+def _oracle_worker_init(barrier, kind: str) -> None:
     """Pool initializer: imports and one small solve (cavity 4), so that no
     worker pays its start-up inside the timed region."""
     _WORKER_BARRIER[0] = barrier
-    _oracle_solve_one(0, dense, 4)
+    _oracle_solve_one(0, kind, 4)
 
 
 def _oracle_worker_sync(_k: int) -> None:
@@ -558,7 +753,7 @@ def _oracle_workers() -> int:
     return 1 if _ORACLE_POOL_FAILED[0] else max(1, len(os.sched_getaffinity(0)))
 
 
-def _oracle_solves(count: int, start_seed: int = 0, dense: bool = False) -> float:
+def _oracle_solves(count: int, start_seed: int = 0, kind: str = "sparse", with_ok: bool = False):
     """Wall seconds for `count` independent JC40 systems solved by the oracle
     on all host cores: one single-threaded worker process per core (spawned,
     so no CUDA state is inherited); the workers' start-up and imports are
@@ -571,20 +766,23 @@ def _oracle_solves(count: int, start_seed: int = 0, dense: bool = False) -> floa
     try:
         mpc = mp.get_context("spawn")
         barrier = mpc.Barrier(workers)
-        with mpc.Pool(workers, initializer=_oracle_worker_init, initargs=(barrier, dense)) as pool:
+        with mpc.Pool(workers, initializer=_oracle_worker_init, initargs=(barrier, kind)) as pool:
             # every worker warm before t0: each of `workers` tasks waits at the barrier until
             # all are taken, so each worker takes exactly one after its initializer has run (a
             # worker lost on the way breaks the barrier instead of leaving the wait hanging)
             pool.map_async(_oracle_worker_sync, range(workers), chunksize=1).get(timeout=180)
             t0 = time.perf_counter()
-            pool.starmap_async(_oracle_solve_one, [(start_seed + k, dense) for k in range(count)],
-                               chunksize=1).get(timeout=300)
-            return time.perf_counter() - t0
+            res = pool.starmap_async(_oracle_solve_one, [(start_seed + k, kind) for k in range(count)],
+                                     chunksize=1).get(timeout=300)
+            dt = time.perf_counter() - t0
+            return (dt, sum(ok for _, ok in res)) if with_ok else dt
     except (OSError, RuntimeError, mp.TimeoutError) as e:   # no worker processes: the same solves, one at a time
         print(f"oracle worker pool unavailable ({e}); timing in this process", file=sys.stderr)
         _ORACLE_POOL_FAILED[0] = True
-        _oracle_solve_one(0, dense, 4)
-        return sum(_oracle_solve_one(start_seed + k, dense) for k in range(count))
+        _oracle_solve_one(0, kind, 4)
+        res = [_oracle_solve_one(start_seed + k, kind) for k in range(count)]
+        dt = sum(t for t, _ in res)
+        return (dt, sum(ok for _, ok in res)) if with_ok else dt
     finally:
         for k, v in saved.items():
             if v is None:
@@ -610,13 +808,20 @@ def _threads():
 def cpu_baseline(sample: int):
     dt = _oracle_solves(sample)
     w = min(_oracle_workers(), sample)
-    _oracle_solve_one(0, True, 4)
-    dd = sum(_oracle_solve_one(s, True) for s in range(2))    # in this process, every BLAS thread
+    ds, ds_ok = _oracle_solves(sample // 2, kind="scipy", with_ok=True)
+    _oracle_solve_one(0, "dense", 4)
+    dd = sum(_oracle_solve_one(s, "dense")[0] for s in range(2))    # in this process, every BLAS thread
     return {"value": sample / dt, "unit": UNIT, "cores": w, "kind": "oracle",
             "sample": f"{sample} JC40 systems (seeds 0..{sample - 1}) by the oracle's sparse CPU pipeline "
                       f"(RCM, iLU(0), BiCGSTAB in FP64 to ||L rho|| <= 1e-10), "
                       + ("in this process" if _ORACLE_POOL_FAILED[0] else f"{w} single-threaded worker processes")
                       + f", {dt:.1f} s",
+            "scipy_spilu_bicgstab": {
+                "value": (sample // 2) / ds, "unit": UNIT, "cores": min(_oracle_workers(), sample // 2),
+                "sample": f"{sample // 2} JC40 systems by SciPy: SciPy RCM, spilu (SuperLU ILUTP, drop 1e-4, fill 10) "
+                          f"and bicgstab to ||b - A x|| <= 5e-11 on the trace-row system, one single-threaded "
+                          f"worker per core, {ds:.1f} s",
+                "reached_tol": int(ds_ok)},
             "dense_lu": {"value": 2 / dd, "unit": UNIT, "cores": _threads(),
                          "sample": f"2 JC40 systems by the oracle's dense FP64 LU (multithreaded BLAS), {dd:.1f} s"}}
 
@@ -660,6 +865,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--serve-rate", type=float, default=300.0)
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

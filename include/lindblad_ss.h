@@ -107,6 +107,10 @@ typedef struct {
     double inner_rtol;     /* SS_PREC_MIXED: relative tolerance of each FP32 inner solve; 1e-5 */
     int lgmres_k;          /* GMRES: corrections of earlier cycles added to each cycle (LGMRES);
                               0 = plain restarted GMRES; restart + lgmres_k <= 64                 */
+    int warm_start;        /* 1: rho_out holds an initial guess on entry (the steady state of a
+                              neighbouring point of a parameter sweep, say): the Krylov iteration
+                              starts from it, scaled to unit trace (inverse power: the start
+                              vector).  A guess of zero trace falls back to the zero start.  0   */
 } ss_options;
 
 /* Per-solve diagnostics. */
@@ -377,6 +381,12 @@ typedef struct {
     double hbm_budget_mb;   /* device memory admitted requests may hold (MiB); <= 0: 80 % of the free memory */
     int max_waves;          /* batches in flight at once (default 4) */
     int max_wave_systems;   /* systems per batch; <= 0: number of SMs / max_waves */
+    int warm_start;         /* 1: a request of the persistent solver starts from the stored steady
+                               state of the earlier request with the same sparsity pattern whose
+                               L~ is closest (by the Frobenius norms of its diagonal and off-diagonal
+                               parts): a parameter sweep then starts every point from a neighbour.
+                               The result is the same steady state within the tolerance, not bit
+                               for bit the result of a cold solve.  Default 0 */
 } ss_server_options;
 
 void ss_server_options_default(ss_server_options* so);
@@ -417,6 +427,19 @@ ss_status ss_profile_read(ss_ctx ctx, int kind, int64_t* launches, double* total
 /* Number of CUDA kernels this library has launched in the process so far
  * (all contexts). */
 unsigned long long ss_launch_count(void);
+/* Limit of every bounded device-side wait issued through this context: a
+ * triangular solve waiting for a row it depends on, a staging barrier of the
+ * batched solver.  Default 2 s; a wait that reaches it makes the call return
+ * SS_ERR_TIMEOUT (the device stays usable).  Tests shorten it to make a
+ * wait run out.  SS_ERR_INVALID for 0. */
+ss_status ss_set_wait_limit(ss_ctx ctx, uint64_t limit_ns);
+/* Failure-detection aid, not part of the paper's method: with restore == 0
+ * the lower triangular solve of M stops computing row `row` (its value is
+ * never written, so the rows depending on it wait until the wait limit and
+ * precond_apply returns SS_ERR_TIMEOUT); restore != 0 undoes it.
+ * SS_ERR_INVALID for a row outside M or a second skipped row. */
+ss_status ss_diag_prec_skip_row(ss_ctx ctx, ss_prec M, int64_t row, int restore);
+
 /* Number of device and pinned-host memory allocations this library has made
  * in the process so far (all contexts): a call that allocates nothing leaves
  * it unchanged. */

@@ -388,7 +388,7 @@ def krylov_solve(A: Matrix, M: Preconditioner, b, x0=None, method: str = "bicgst
 
 
 def _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed,
-             inner_rtol=1e-5, lgmres_k=0):
+             inner_rtol=1e-5, lgmres_k=0, warm_start=0):
     opt = B.Options()
     B.load().ss_options_default(C.byref(opt))
     opt.method = B.METHODS[method]
@@ -399,6 +399,7 @@ def _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_f
     opt.use_rcm, opt.seed = int(bool(use_rcm)), seed
     opt.inner_rtol = inner_rtol
     opt.lgmres_k = lgmres_k
+    opt.warm_start = int(bool(warm_start))
     return opt
 
 
@@ -406,9 +407,12 @@ def steady_state_batched(systems: Sequence, method: str = "iterative-bicgstab", 
                          precond: str = "ilu0", precision: str = "fp64", maxiter: int = 1000, restart: int = 30,
                          drop_tol: float = 1e-4, fill_factor: float = 10.0, w: float = 0.0, sigma: float = 1e-15,
                          use_rcm: bool = True, seed: int = 0, ctx: Optional[Context] = None,
-                         raise_on_failure: bool = True, inner_rtol: float = 1e-5, lgmres_k: int = 0):
+                         raise_on_failure: bool = True, inner_rtol: float = 1e-5, lgmres_k: int = 0,
+                         rho_init: Optional[Sequence] = None):
     """Steady states of many systems, each given as (H, c_ops); returns a list
-    of rho (numpy, d x d) and a list of info dicts."""
+    of rho (numpy, d x d) and a list of info dicts.  rho_init: optional
+    initial guesses (one d x d matrix per system, e.g. the steady states of
+    neighbouring sweep points): the solves start from them (warm start)."""
     ctx = ctx or get_context()
     hosts = [(_CsrHost(H), [_CsrHost(c) for c in cs]) for H, cs in systems]
     ns = len(hosts)
@@ -417,10 +421,13 @@ def steady_state_batched(systems: Sequence, method: str = "iterative-bicgstab", 
     carrs = [(B.CsrView * max(len(cs), 1))(*[c.view for c in cs]) for _, cs in hosts]
     cptrs = (C.POINTER(B.CsrView) * max(ns, 1))(*[C.cast(a, C.POINTER(B.CsrView)) for a in carrs])
     rhos = [np.empty(h.view.n_rows ** 2, dtype=np.complex128) for h, _ in hosts]
+    if rho_init is not None:
+        for r, r0 in zip(rhos, rho_init):
+            r[:] = np.asarray(r0, dtype=np.complex128).reshape(-1, order="F")
     outs = (C.c_void_p * max(ns, 1))(*[r.ctypes.data for r in rhos])
     infos = (B.Info * max(ns, 1))()
     opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed,
-                   inner_rtol, lgmres_k)
+                   inner_rtol, lgmres_k, rho_init is not None)
     st = B.load().steady_state_batched(ctx.handle, ns, Hs, ncs, cptrs, C.byref(opt), outs, 0, infos)
     if st != 0 and (raise_on_failure or st not in (B.SS_NOT_CONVERGED, B.SS_BREAKDOWN)):
         ctx.check(st, "steady_state_batched")
@@ -445,8 +452,10 @@ def steady_state(H, c_ops: Sequence, method: str = "iterative-bicgstab", tol: fl
                  precond: str = "ilu0", precision: str = "fp64", maxiter: int = 1000, restart: int = 30,
                  drop_tol: float = 1e-4, fill_factor: float = 10.0, w: float = 0.0, sigma: float = 1e-15,
                  use_rcm: bool = True, seed: int = 0, ctx: Optional[Context] = None, out=None,
-                 raise_on_failure: bool = True, inner_rtol: float = 1e-5, lgmres_k: int = 0):
+                 raise_on_failure: bool = True, inner_rtol: float = 1e-5, lgmres_k: int = 0, rho_init=None):
     """rho_ss (d x d complex128, trace one) and the solve's info dict.
+    rho_init: optional initial guess (d x d), e.g. a neighbouring sweep
+    point's steady state (warm start).
 
     out: optional CUDA complex128 tensor of d*d elements (column-major rho);
     when given, rho is written there and returned as a (d, d) view (transposed
@@ -457,14 +466,19 @@ def steady_state(H, c_ops: Sequence, method: str = "iterative-bicgstab", tol: fl
     cvs = [_CsrHost(c) for c in c_ops]
     arr = (B.CsrView * max(len(cvs), 1))(*[c.view for c in cvs])
     opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed,
-                   inner_rtol, lgmres_k)
+                   inner_rtol, lgmres_k, rho_init is not None)
     d = hv.view.n_rows
     info = B.Info()
     if out is None:
         rho = np.empty(d * d, dtype=np.complex128)
+        if rho_init is not None:
+            rho[:] = np.asarray(rho_init, dtype=np.complex128).reshape(-1, order="F")
         ptr, on_dev = rho.ctypes.data, 0
     else:
         ptr, on_dev = _dev_ptr(out, "c128", d * d), 1
+        if rho_init is not None:
+            import torch
+            out.copy_(torch.as_tensor(np.asarray(rho_init, dtype=np.complex128).reshape(-1, order="F")))
     st = B.load().steady_state(ctx.handle, C.byref(hv.view), len(cvs), arr, C.byref(opt), ptr, on_dev,
                                C.byref(info))
     if st != 0 and (raise_on_failure or st not in (B.SS_NOT_CONVERGED, B.SS_BREAKDOWN)):
@@ -483,7 +497,7 @@ class Server:
                  precision: str = "mixed", maxiter: int = 1000, restart: int = 30, drop_tol: float = 1e-4,
                  fill_factor: float = 10.0, w: float = 0.0, sigma: float = 1e-15, use_rcm: bool = True,
                  seed: int = 0, inner_rtol: float = 1e-5, hbm_budget_mb: float = 0.0, max_waves: int = 4,
-                 max_wave_systems: int = 0, device: int = 0, lgmres_k: int = 0):
+                 max_wave_systems: int = 0, device: int = 0, lgmres_k: int = 0, warm_start: bool = False):
         lib = B.load()
         opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm,
                        seed, inner_rtol, lgmres_k)
@@ -492,6 +506,7 @@ class Server:
         so.hbm_budget_mb = hbm_budget_mb
         so.max_waves = max_waves
         so.max_wave_systems = max_wave_systems
+        so.warm_start = int(bool(warm_start))
         h = C.c_void_p()
         st = lib.ss_server_create(device, C.byref(opt), C.byref(so), C.byref(h))
         if st != 0:

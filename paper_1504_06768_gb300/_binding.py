@@ -34,7 +34,8 @@ class Options(C.Structure):
     _fields_ = [("method", C.c_int), ("precond", C.c_int), ("precision", C.c_int), ("tol", C.c_double),
                 ("maxiter", C.c_int), ("restart", C.c_int), ("drop_tol", C.c_double),
                 ("fill_factor", C.c_double), ("w", C.c_double), ("sigma", C.c_double),
-                ("use_rcm", C.c_int), ("seed", C.c_uint64), ("inner_rtol", C.c_double), ("lgmres_k", C.c_int)]
+                ("use_rcm", C.c_int), ("seed", C.c_uint64), ("inner_rtol", C.c_double), ("lgmres_k", C.c_int),
+                ("warm_start", C.c_int)]
 
 
 class Info(C.Structure):
@@ -59,7 +60,8 @@ _I32P = C.POINTER(C.c_int32)
 _DP = C.POINTER(C.c_double)
 
 class ServerOptions(C.Structure):
-    _fields_ = [("hbm_budget_mb", C.c_double), ("max_waves", C.c_int), ("max_wave_systems", C.c_int)]
+    _fields_ = [("hbm_budget_mb", C.c_double), ("max_waves", C.c_int), ("max_wave_systems", C.c_int),
+                ("warm_start", C.c_int)]
 
 
 _SIGNATURES = {
@@ -97,6 +99,8 @@ _SIGNATURES = {
     "ss_profile_read": (C.c_int, [_P, C.c_int, _I64P, _DP]),
     "ss_launch_count": (C.c_ulonglong, []),
     "ss_alloc_count": (C.c_ulonglong, []),
+    "ss_set_wait_limit": (C.c_int, [_P, C.c_uint64]),
+    "ss_diag_prec_skip_row": (C.c_int, [_P, _P, C.c_int64, C.c_int]),
     "lgmres_solve": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int, C.c_int, C.c_int,
                                C.POINTER(C.c_int), _DP]),
     "ss_rcm_order_host": (C.c_int, [C.c_int64, _P, _P, _P]),

@@ -149,6 +149,7 @@ extern "C" void ss_options_default(ss_options* o) {
     o->seed = 0;
     o->inner_rtol = 1e-5;
     o->lgmres_k = 0;
+    o->warm_start = 0;
 }
 
 // ----------------------------------------------------------------- matrices
@@ -303,6 +304,9 @@ extern "C" void ss_mat_free(ss_mat A) {
     dev_free_nostream(A->m.val);
     dev_free_nostream(A->diag_pos);
     dev_free_nostream(A->val32);
+    dev_free_nostream(A->m.s_row_ptr);
+    dev_free_nostream(A->m.s_col);
+    dev_free_nostream(A->m.s_val);
     cudaStreamSynchronize(0);
     delete A;
 }
@@ -310,6 +314,7 @@ extern "C" void ss_mat_free(ss_mat A) {
 extern "C" ss_status spmv(ss_ctx ctx, ss_mat A, const double* x, double* y) {
     SS_TRY(check_ctx(ctx));
     if (!A || !x || !y) return set_error(ctx, SS_ERR_INVALID, "null argument");
+    SS_TRY(csr_split(ctx, A->m));
     SS_TRY(spmv_dev(ctx, A->m, reinterpret_cast<const double2*>(x), reinterpret_cast<double2*>(y)));
     SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return SS_OK;
@@ -379,6 +384,18 @@ extern "C" ss_status precond_apply_f32(ss_ctx ctx, ss_prec M, const float* r, fl
     return prec_check_error(ctx, M);
 }
 
+extern "C" ss_status ss_set_wait_limit(ss_ctx ctx, uint64_t limit_ns) {
+    if (!ctx || limit_ns == 0) return SS_ERR_INVALID;
+    ctx->wait_ns = limit_ns;
+    return SS_OK;
+}
+
+extern "C" ss_status ss_diag_prec_skip_row(ss_ctx ctx, ss_prec M, int64_t row, int restore) {
+    SS_TRY(check_ctx(ctx));
+    if (!M) return set_error(ctx, SS_ERR_INVALID, "null argument");
+    return prec_skip_row(ctx, M, row, restore);
+}
+
 extern "C" ss_status ss_prec_info(ss_prec M, int64_t* nnz, int32_t* levels_lower, int32_t* levels_upper) {
     if (!M) return SS_ERR_INVALID;
     if (nnz) *nnz = M->f.nnz;
@@ -416,6 +433,7 @@ extern "C" ss_status krylov_solve(ss_ctx ctx, ss_mat A, ss_prec M, int krylov, c
     SS_TRY(check_ctx(ctx));
     if (!A || !M || !b || !x) return set_error(ctx, SS_ERR_INVALID, "null argument");
     if (M->f.n_rows != A->m.n_rows) return set_error(ctx, SS_ERR_INVALID, "preconditioner size mismatch");
+    SS_TRY(csr_split(ctx, A->m));
     KrylovWork w;
     const int m = krylov == SS_KRYLOV_GMRES ? restart : 0;
     ss_status st = krylov_workspace(ctx, w, A->m.n_rows, krylov, m);
@@ -444,6 +462,7 @@ extern "C" ss_status lgmres_solve(ss_ctx ctx, ss_mat A, ss_prec M, const double*
     SS_TRY(check_ctx(ctx));
     if (!A || !M || !b || !x) return set_error(ctx, SS_ERR_INVALID, "null argument");
     if (M->f.n_rows != A->m.n_rows) return set_error(ctx, SS_ERR_INVALID, "preconditioner size mismatch");
+    SS_TRY(csr_split(ctx, A->m));
     KrylovWork w;
     ss_status st = krylov_workspace(ctx, w, A->m.n_rows, SS_KRYLOV_GMRES, restart, augment);
     KrylovResultHost res;
@@ -606,6 +625,7 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
     if (direct) return steady_state_direct(ctx, Ap, perm, d, w_used, opt, t0, inf, rho_out, rho_on_device, info);
     st = build_prec(ctx, Ap->m, opt.precond, opt.drop_tol, opt.fill_factor, mixed, &M);
     if (st == SS_OK && mixed) st = ensure_f32(ctx, Ap);
+    if (st == SS_OK) st = csr_split(ctx, Ap->m);
     if (st != SS_OK) { ss_mat_free(Ap); return st; }
     inf.nnz_factors = M->f.nnz;
     inf.levels_lower = M->lower.n_levels;
@@ -639,6 +659,13 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
     SS_CUDA(ctx, cudaMemcpyAsync(tidx_d, tidx.data(), sizeof(int32_t) * d, cudaMemcpyHostToDevice, ctx->stream));
     STEP(su_condest(ctx, M, n, y, x, scr, &inf.condest));
     STEP(krylov_workspace(ctx, kw, n, krylov, krylov == SS_KRYLOV_GMRES ? opt.restart : 0, kaug));
+    // warm start: the caller's guess (natural order, in rho_out) arrives in `rho`
+    if (opt.warm_start)
+        SS_CUDA(ctx, cudaMemcpyAsync(rho, rho_out, sizeof(double2) * n,
+                                     rho_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    auto initial = [&](double2* v) {
+        return opt.warm_start ? su_warm_start(ctx, n, d, perm_d, rho, trace_d, v) : su_zero(ctx, n, v);
+    };
     const double t1 = now_ms();
 
     double lr = INFINITY;
@@ -650,7 +677,7 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
         STEP(su_zero(ctx, n, b));
         double2 wb = make_double2(w_used, 0.0);
         SS_CUDA(ctx, cudaMemcpyAsync(b + r0, &wb, sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
-        STEP(su_zero(ctx, n, x));
+        STEP(initial(x));
         double2* r64 = nullptr;
         float2 *b32 = nullptr, *x32 = nullptr;
         STEP(dev_alloc_n(ctx, &r64, (size_t)n));
@@ -681,7 +708,7 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
         STEP(su_zero(ctx, n, b));
         double2 wb = make_double2(w_used, 0.0);
         SS_CUDA(ctx, cudaMemcpyAsync(b + r0, &wb, sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
-        STEP(su_zero(ctx, n, x));
+        STEP(initial(x));
         double inner = 0.5 * opt.tol;
         outer = 1;
         for (int pass = 0; pass < 8; ++pass) {
@@ -702,7 +729,8 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
         }
     } else {
         // x_0 random (SplitMix64 counters), ||x_0|| = 1; b holds x_k, x holds v
-        STEP(su_start_vector(ctx, n, opt.seed, perm_d, b));
+        if (opt.warm_start) STEP(initial(b));
+        else STEP(su_start_vector(ctx, n, opt.seed, perm_d, b));
         STEP(su_normalise(ctx, n, b, scr));
         double2* oc_y = nullptr;
         double* oc_scr = nullptr;

@@ -244,6 +244,69 @@ void PatternCache::insert(const PatternKey& k, const std::shared_ptr<Pattern>& p
     }
 }
 
+const SolutionCache::Entry* SolutionCache::nearest(const PatternKey& k, double2 fp) {
+    auto it = by_key.find(k);
+    if (it == by_key.end()) return nullptr;
+    const Entry* best = nullptr;
+    double bd = INFINITY;
+    for (const Entry& e : it->second) {
+        const double dd = std::fabs(e.fp.x - fp.x) / std::max(std::max(e.fp.x, fp.x), 1e-300) +
+                          std::fabs(e.fp.y - fp.y) / std::max(std::max(e.fp.y, fp.y), 1e-300);
+        if (dd < bd) {
+            bd = dd;
+            best = &e;
+        }
+    }
+    return best;
+}
+
+ss_status SolutionCache::insert(ss_ctx ctx, const PatternKey& k, double2 fp, const double2* rho, int64_t n) {
+    std::lock_guard<std::mutex> lock(mu);
+    const size_t sz = sizeof(double2) * (size_t)n;
+    if (sz > max_bytes) return SS_OK;
+    auto evict_oldest = [&](std::vector<Entry>* only) {
+        std::vector<Entry>* from = nullptr;
+        size_t at = 0;
+        uint64_t oldest = UINT64_MAX;
+        for (auto& kv : by_key) {
+            if (only && &kv.second != only) continue;
+            for (size_t i = 0; i < kv.second.size(); ++i)
+                if (kv.second[i].stamp < oldest) {
+                    oldest = kv.second[i].stamp;
+                    from = &kv.second;
+                    at = i;
+                }
+        }
+        if (!from) return false;
+        dev_free(ctx, (*from)[at].rho);
+        bytes -= sizeof(double2) * (size_t)(*from)[at].n;
+        from->erase(from->begin() + (ptrdiff_t)at);
+        return true;
+    };
+    std::vector<Entry>& v = by_key[k];
+    while (v.size() >= per_key && evict_oldest(&v)) {
+    }
+    while (bytes + sz > max_bytes && evict_oldest(nullptr)) {
+    }
+    Entry e;
+    e.fp = fp;
+    e.n = n;
+    e.stamp = ++clock;
+    SS_TRY(dev_alloc_n(ctx, &e.rho, (size_t)n));
+    SS_CUDA(ctx, cudaMemcpyAsync(e.rho, rho, sz, cudaMemcpyDeviceToDevice, ctx->stream));
+    bytes += sz;
+    by_key[k].push_back(e);
+    return SS_OK;
+}
+
+void SolutionCache::clear(ss_ctx ctx) {
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& kv : by_key)
+        for (Entry& e : kv.second) dev_free(ctx, e.rho);
+    by_key.clear();
+    bytes = 0;
+}
+
 size_t wave_footprint_bytes(int64_t d, int64_t nnz_h, const std::vector<int64_t>& nnz_c,
                             const std::vector<int64_t>& ctc_c, bool mixed) {
     // nnz(L) <= 2 d nnz(H) + sum_k (nnz(C_k)^2 + 2 d nnz(C_k^+ C_k)) + d (trace row), the
@@ -379,6 +442,15 @@ ss_status wave_begin(BatchWave& w) {
             for (size_t p : fresh) w.cache->insert(rep_key[p], w.pats[p]);
         }
     }
+    w.key_of.resize(ns);
+    for (size_t q = 0; q < ns; ++q) w.key_of[q] = rep_key[w.pat_of[q]];
+    // the queue takes the systems by estimated cost, largest first
+    std::vector<int32_t> order;
+    WSTEP(batch_cost_order(ctx, blt, order, &w.fp));
+    int32_t* order_d = nullptr;
+    WSTEP(dev_alloc_n(ctx, &order_d, ns));
+    w.owned.push_back(order_d);
+    SS_CUDA(ctx, cudaMemcpyAsync(order_d, order.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, ctx->stream));
     // (3) per-system buffers (one allocation) and descriptors; describe() lays
     // out system q's buffers from address base and returns the bytes used
     const size_t inner = mixed ? sizeof(float2) : sizeof(double2);
@@ -446,6 +518,28 @@ ss_status wave_begin(BatchWave& w) {
     w.owned.push_back(blk_all);
     for (size_t q = 0; q < ns; ++q) describe(q, reinterpret_cast<uintptr_t>(blk_all) + boff[q], w.hs[q], gather[q]);
     WSTEP(batch_gather_values(ctx, blt, gather));
+    // warm starts: the caller's guesses (in rho_out), or, in the serving loop,
+    // the stored state of the closest earlier request with the same pattern
+    bool cache_copies = false;
+    for (size_t q = 0; q < ns; ++q) {
+        if (opt.warm_start) {
+            w.hs[q].warm = 1;
+            if (!w.rho_on_device)
+                SS_CUDA(ctx, cudaMemcpyAsync(w.hs[q].rho_out, w.rho_out[q], sizeof(double2) * blt.n[q],
+                                             cudaMemcpyHostToDevice, ctx->stream));
+        } else if (w.sols) {
+            std::lock_guard<std::mutex> lock(w.sols->mu);
+            const SolutionCache::Entry* e = w.sols->nearest(w.key_of[q], w.fp[q]);
+            if (e && e->n == blt.n[q]) {
+                SS_CUDA(ctx, cudaMemcpyAsync(w.hs[q].rho_out, e->rho, sizeof(double2) * e->n, cudaMemcpyDeviceToDevice,
+                                             ctx->stream));
+                w.hs[q].warm = 1;
+                cache_copies = true;
+            }
+        }
+    }
+    // a stored state may be evicted by a later wave: its copy is complete before this wave goes on
+    if (cache_copies) SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     WSTEP(dev_alloc_n(ctx, &w.dsys, ns));
     w.owned.push_back(w.dsys);
     WSTEP(dev_alloc_n(ctx, &w.ctl, 4));
@@ -455,6 +549,8 @@ ss_status wave_begin(BatchWave& w) {
     w.t1 = now_ms();
 
     BatchParams bp;
+    std::memset(&bp, 0, sizeof(bp));
+    bp.order = order_d;
     bp.tol = opt.tol;
     bp.maxiter = opt.maxiter;
     bp.mixed = mixed ? 1 : 0;
@@ -529,6 +625,14 @@ ss_status wave_end(BatchWave& w, ss_info* infos) {
         return cuda_check(ctx, e, "steady_state_batched");
     }
     w.t2 = now_ms();
+    if (w.sols && !herr) {
+        for (size_t q = 0; q < ns; ++q)
+            if (w.hs[q].status == SS_OK) {
+                ss_status cs = w.sols->insert(ctx, w.key_of[q], w.fp[q], w.hs[q].rho_out, w.blt.n[q]);
+                if (cs != SS_OK) break;           // the cache is an aid: a failed copy only ends its filling
+            }
+        cudaStreamSynchronize(ctx->stream);
+    }
     ss_status worst = SS_OK;
     for (size_t q = 0; q < ns; ++q) {
         const Pattern& P = *w.pats[w.pat_of[q]];

@@ -522,3 +522,64 @@ ss_status batch_verify_against(ss_ctx ctx, const BatchLt& b, int s, const int32_
     if (ce != cudaSuccess) return cuda_check(ctx, ce, "pattern verification");
     return SS_OK;
 }
+
+// ------------------------------------------------------- cost estimate
+
+namespace {
+
+// Per system: the squared Frobenius norms of the diagonal and of the
+// off-diagonal entries of L~ (one block per system, fixed-order sums).
+__global__ void diag_offdiag_b(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                               const double2* __restrict__ val, const int64_t* __restrict__ row_off,
+                               const BatchMeta* __restrict__ meta, double2* __restrict__ out) {
+    const int64_t s = blockIdx.x;
+    const int64_t n = row_off[s + 1] - row_off[s];
+    const int32_t* lrp = rp + row_off[s] + s;
+    const int32_t* lcol = col + meta[s].nz_off;
+    const double2* lval = val + meta[s].nz_off;
+    double dg = 0.0, off = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x)
+        for (int32_t t = lrp[r]; t < lrp[r + 1]; ++t) {
+            const double m2 = lval[t].x * lval[t].x + lval[t].y * lval[t].y;
+            if (lcol[t] == r) dg += m2; else off += m2;
+        }
+    __shared__ double sd[256], so[256];
+    sd[threadIdx.x] = dg;
+    so[threadIdx.x] = off;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            sd[threadIdx.x] += sd[threadIdx.x + h];
+            so[threadIdx.x] += so[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[s] = make_double2(sd[0], so[0]);
+}
+
+}  // namespace
+
+ss_status batch_cost_order(ss_ctx ctx, const BatchLt& b, std::vector<int32_t>& order, std::vector<double2>* fp) {
+    const int64_t ns = b.ns;
+    order.resize(ns);
+    for (int64_t s = 0; s < ns; ++s) order[s] = (int32_t)s;
+    if (ns == 0) return SS_OK;
+    double2* nd = nullptr;
+    SS_TRY(dev_alloc_n(ctx, &nd, (size_t)ns));
+    std::vector<double2> h(ns);
+    diag_offdiag_b<<<(ss_count_launch(), (unsigned)ns), 256, 0, ctx->stream>>>(b.rp, b.col, b.val, b.row_off_d,
+                                                                             b.meta_d, nd);
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h.data(), nd, sizeof(double2) * ns, cudaMemcpyDeviceToHost, ctx->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, nd);
+    if (ce != cudaSuccess) return cuda_check(ctx, ce, "cost estimate");
+    if (fp) fp->assign(h.begin(), h.end());
+    std::vector<double> cost(ns);
+    for (int64_t s = 0; s < ns; ++s) {
+        const double ratio = h[s].x > 0.0 ? std::sqrt(h[s].y / h[s].x) : 1.0;
+        cost[s] = (double)b.meta[s].nnz * (1.0 + ratio);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) { return cost[a] > cost[c]; });
+    return SS_OK;
+}

@@ -66,6 +66,31 @@ struct PatternCache {
     void insert(const PatternKey& k, const std::shared_ptr<Pattern>& p);
 };
 
+// Steady states of earlier requests kept on the device by the serving loop,
+// per sparsity pattern, each with the fingerprint of its L~ (squared
+// Frobenius norms of the diagonal and the off-diagonal part): a new request
+// of the same pattern starts from the stored state with the closest
+// fingerprint (a neighbouring point of a parameter sweep).  Bounded in
+// entries per pattern and in bytes; the oldest entry goes first.
+struct SolutionCache {
+    struct Entry {
+        double2 fp;                   // (||diag||^2, ||offdiag||^2) of L~
+        double2* rho = nullptr;       // device, natural column-major order, n values
+        int64_t n = 0;
+        uint64_t stamp = 0;
+    };
+    std::mutex mu;
+    std::map<PatternKey, std::vector<Entry>> by_key;
+    size_t bytes = 0, max_bytes = (size_t)256 << 20;
+    size_t per_key = 8;
+    uint64_t clock = 0;
+    // the closest entry of key k to fingerprint fp (null: none)
+    const Entry* nearest(const PatternKey& k, double2 fp);
+    // stores a copy of rho (device, on ctx's stream), evicting old entries
+    ss_status insert(ss_ctx ctx, const PatternKey& k, double2 fp, const double2* rho, int64_t n);
+    void clear(ss_ctx ctx);
+};
+
 struct BatchWave {
     // inputs (borrowed for the duration of wave_begin; the views' arrays are read there)
     ss_ctx ctx = nullptr;                 // its stream carries the wave
@@ -76,10 +101,13 @@ struct BatchWave {
     int rho_on_device = 0;
     bool stage_pinned = false;            // host results: copy through pinned memory, asynchronously
     PatternCache* cache = nullptr;
+    SolutionCache* sols = nullptr;        // serving: warm starts from earlier requests (null: off)
     // state
     BatchLt blt;
     std::vector<std::shared_ptr<Pattern>> pats;
     std::vector<int> pat_of;
+    std::vector<PatternKey> key_of;       // per system: its pattern's cache key
+    std::vector<double2> fp;              // per system: fingerprint of L~ (see SolutionCache)
     std::vector<void*> owned;
     std::vector<BatchSys> hs;
     BatchSys* dsys = nullptr;

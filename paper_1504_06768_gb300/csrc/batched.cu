@@ -112,16 +112,24 @@ struct UnitRegs {
     int32_t jj[MAXE];
     T vv[MAXE];
     int32_t i, ob, oe;
+    T dv;                           // upper triangle: 1 / u_ii of the lane's row (packed, prefetched with the unit)
 };
 
+template <class T>
+__host__ __device__ __forceinline__ int dinv_stride(int R);
+
+// with_dinv: also fetch the row's 1 / u_ii from the packed upper operand, so
+// that no global load stays on the critical path of an upper level.
 template <int G, class T>
-__device__ __forceinline__ void load_unit(const PackedOp& P, int32_t u, int lane, UnitRegs<T>& r) {
+__device__ __forceinline__ void load_unit(const PackedOp& P, int32_t u, int lane, UnitRegs<T>& r,
+                                          bool with_dinv = false) {
     constexpr int R = 32 / G;
     const T* __restrict__ pv = reinterpret_cast<const T*>(P.val);
     const int E = P.E;
     const int grp = lane / G;
     r.i = -1;
     r.ob = r.oe = 0;
+    r.dv = zero<T>();
 #pragma unroll
     for (int q = 0; q < MAXE; ++q) {
         r.jj[q] = -1;
@@ -139,6 +147,10 @@ __device__ __forceinline__ void load_unit(const PackedOp& P, int32_t u, int lane
             r.jj[q] = P.col[slot];
             r.vv[q] = pv[slot];
         }
+    if (with_dinv && (lane % G) == 0) {
+        const int ds = dinv_stride<T>(R) / (int)sizeof(T);
+        r.dv = reinterpret_cast<const T*>(P.dinv)[(int64_t)u * ds + grp];
+    }
 }
 
 // Row update of a triangular solve on the shared vector buf: LOWER:
@@ -326,8 +338,9 @@ __device__ void cta_trsv_ring(const PackedOp& P, const int32_t* lvl, const int32
             const uint32_t q = s0 + l;
             const int slot = q % ns;
             const int32_t end = lvl[l + 1], cnt = end - beg;
-            if (warp < cnt) {                       // warps without a unit do not read the slot
-                ring_wait(rg, slot, (q / ns) & 1u);
+            // warps without a unit do not read the slot; after an abandoned wait
+            // (the block is aborting) the slot's contents are not valid and are not read
+            if (warp < cnt && (ring_wait(rg, slot, (q / ns) & 1u), *(volatile int*)rg.abort == 0)) {
                 const unsigned char* sb = reinterpret_cast<const unsigned char*>(sv0) + (size_t)slot * rg.slot_bytes;
                 const T* sv = reinterpret_cast<const T*>(sb) + lane;
                 const int32_t* sc = reinterpret_cast<const int32_t*>(sb + sl.col) + lane;
@@ -382,17 +395,19 @@ template <bool LOWER, int G, class T>
 __device__ void cta_trsv_pk(const PackedOp& P, const int32_t* lvl, const int32_t* __restrict__ ocol,
                             const T* __restrict__ oval, const T* __restrict__ inv, T* buf) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane % G;
+    const bool dv = !LOWER && P.dinv != nullptr;   // packed 1 / u_ii, else from inv[] (global, on the level's path)
     UnitRegs<T> ua, ub;
     int32_t beg = lvl[0], end = lvl[1];
-    load_unit<G, T>(P, beg + warp < end ? beg + warp : P.nunits, lane, ua);
+    load_unit<G, T>(P, beg + warp < end ? beg + warp : P.nunits, lane, ua, dv);
     for (int32_t l = 0; l < P.nlev; ++l) {
         const int32_t nb = end, ne = (l + 1 < P.nlev) ? lvl[l + 2] : end;
-        load_unit<G, T>(P, nb + warp < ne ? nb + warp : P.nunits, lane, ub);
-        solve_row<LOWER, G, T>(ua, (!LOWER && ua.i >= 0) ? inv[ua.i] : zero<T>(), ocol, oval, buf, sub);
+        load_unit<G, T>(P, nb + warp < ne ? nb + warp : P.nunits, lane, ub, dv);
+        solve_row<LOWER, G, T>(ua, LOWER || ua.i < 0 ? zero<T>() : (dv ? ua.dv : inv[ua.i]), ocol, oval, buf, sub);
         for (int32_t u = beg + warp + NW; u < end; u += NW) {      // wide levels: more units per warp
             UnitRegs<T> uc;
-            load_unit<G, T>(P, u, lane, uc);
-            solve_row<LOWER, G, T>(uc, (!LOWER && uc.i >= 0) ? inv[uc.i] : zero<T>(), ocol, oval, buf, sub);
+            load_unit<G, T>(P, u, lane, uc, dv);
+            solve_row<LOWER, G, T>(uc, LOWER || uc.i < 0 ? zero<T>() : (dv ? uc.dv : inv[uc.i]), ocol, oval, buf,
+                                   sub);
         }
         __syncthreads();
         ua = ub;
@@ -818,6 +833,27 @@ __device__ bool cta_ilu0(const BatchSys& S, bool mixed) {
 }
 
 // ------------------------------------------------------------- drivers
+// Initial iterate x (FP64, permuted order): zero, or with a warm start the
+// caller's rho (natural column-major order, in rho_out) scaled to unit trace,
+// the normalisation the solution of Eq. (linear) has.  A guess of zero trace
+// gives the zero start.
+__device__ void cta_initial_guess(const BatchSys& S, bool warm, double2* x, double* red) {
+    double tr[2] = {0.0, 0.0};
+    if (warm) {
+        for (int32_t i = threadIdx.x; i < S.d; i += BT) {
+            const double2 v = S.rho_out[(int64_t)i * (S.d + 1)];
+            tr[0] += v.x;
+            tr[1] += v.y;
+        }
+        cta_sum<2>(tr, red);
+    }
+    const bool use = warm && (tr[0] != 0.0 || tr[1] != 0.0);
+    const double2 t = make_double2(tr[0], tr[1]);
+    for (int32_t r = threadIdx.x; r < S.n; r += BT)
+        x[r] = use ? cdiv(S.rho_out[S.perm[r]], t) : make_double2(0.0, 0.0);
+    __syncthreads();
+}
+
 __device__ void solve_fp64(BatchSys& S, const BatchParams& P, SmemPlan& sm, double* red) {
     const int32_t n = S.n;
     Ctx<double2> c;
@@ -834,11 +870,8 @@ __device__ void solve_fp64(BatchSys& S, const BatchParams& P, SmemPlan& sm, doub
     double2* wk = reinterpret_cast<double2*>(S.work);
     double2* b = wk + 8 * (size_t)n;
     double2* x = S.x64;
-    for (int32_t i = threadIdx.x; i < n; i += BT) {
-        b[i] = make_double2(i == S.r0 ? S.w : 0.0, 0.0);
-        x[i] = make_double2(0.0, 0.0);
-    }
-    __syncthreads();
+    for (int32_t i = threadIdx.x; i < n; i += BT) b[i] = make_double2(i == S.r0 ? S.w : 0.0, 0.0);
+    cta_initial_guess(S, S.warm != 0, x, red);
     double inner = 0.5 * P.tol, lr = INFINITY;
     int total = 0, status = SS_NOT_CONVERGED;
     for (int pass = 0; pass < 8; ++pass) {
@@ -927,11 +960,8 @@ __device__ void solve_mixed(BatchSys& S, const BatchParams& P, SmemPlan& sm, dou
     T* ph = sm.pbuf ? reinterpret_cast<T*>(sm.pbuf) : phat;     // p^: shared memory when it fits
     double2* x = S.x64;
     double2* r64 = S.r64;
-    for (int32_t i = threadIdx.x; i < n; i += BT) {
-        x[i] = make_double2(0.0, 0.0);
-        xd[i] = make_float2(0.f, 0.f);
-    }
-    __syncthreads();
+    for (int32_t i = threadIdx.x; i < n; i += BT) xd[i] = make_float2(0.f, 0.f);
+    cta_initial_guess(S, S.warm != 0, x, red);
     // x += xd in FP64, xd = 0
     auto fold = [&]() {
         for (int32_t i = threadIdx.x; i < n; i += BT) {
@@ -1142,7 +1172,10 @@ __global__ void __launch_bounds__(BT, BATCH_BLOCKS_PER_SM) batched_solver(BatchS
     uint32_t ring_seq = 0;          // levels staged by this block (identical in every thread)
     Ring last{};
     while (true) {
-        if (threadIdx.x == 0) s_idx = atomicAdd(queue, 1);
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(queue, 1);
+            s_idx = (t < nsys && P.order) ? P.order[t] : t;
+        }
         __syncthreads();
         const int k = s_idx;
         __syncthreads();

@@ -48,6 +48,7 @@ struct BatchSys {
     float2* f_val32;
     float2* f_inv32;
     int32_t factor_on_device;   // 1: iLU(0) computed in the kernel from a_val; 0: factors given
+    int32_t warm;               // 1: rho_out holds the initial guess (natural order, column-major)
     // packed operands of the two triangular solves and of the SpMV
     PackedOp lo, up, pa;
     const int32_t* lvl_ptr;     // lower level boundaries in lvl_rows (factorisation schedule)
@@ -77,6 +78,7 @@ struct BatchParams {
     int power;                  // inverse power (FP64 only)
     uint64_t seed;
     int ring_allowed;           // every staged array is 16-byte aligned (bulk copies may be used)
+    const int32_t* order;       // device: the k-th system taken is order[k] (null: submission order)
     // shared-memory plan of the launch (set by batch_launch)
     int ring_umax;              // units per staged level (0: no ring)
     int ring_slots;             // slots of the ring
@@ -137,6 +139,16 @@ ss_status batch_gather_values(ss_ctx ctx, const BatchLt& b, const std::vector<Ga
 // (rp_d: n + 1 row pointers, col_d: nnz columns) on the device.
 ss_status batch_verify_against(ss_ctx ctx, const BatchLt& b, int s, const int32_t* rp_d, const int32_t* col_d,
                                int* mismatch);
+
+// Order in which the persistent solver takes the systems: largest estimated
+// cost first (longest-processing-time-first list scheduling, so that no long
+// system starts last and holds one SM while the others idle).  The estimate
+// is the entry count of L~ times (1 + ||offdiag(L~)||_F / ||diag(L~)||_F):
+// iLU(0)-preconditioned Krylov methods need more iterations the weaker the
+// diagonal.  Ties keep the submission order.  Results do not depend on it.
+// fp (may be null) receives each system's (||diag||_F^2, ||offdiag||_F^2).
+ss_status batch_cost_order(ss_ctx ctx, const BatchLt& b, std::vector<int32_t>& order,
+                           std::vector<double2>* fp = nullptr);
 
 int batch_max_n(bool mixed);
 // Chooses the shared-memory plan (ring size, level boundaries in shared

@@ -50,6 +50,17 @@ struct DeviceCSR {          // complex FP64 CSR on the device
     int32_t* row_ptr = nullptr;
     int32_t* col = nullptr;
     double2* val = nullptr;
+    // Part-split copy for the FP64 SpMV (built on demand by csr_split): each
+    // stored entry becomes one real "part" per nonzero component, s_col
+    // holding its column with bit 31 set for an imaginary part.  Entries of
+    // the Liouvillian are mostly purely real (dissipators) or purely
+    // imaginary (the Hamiltonian commutator), so a part costs 12 bytes and
+    // 2 FMAs where a complex entry costs 20 bytes and 4 FMAs.
+    int32_t* s_row_ptr = nullptr;
+    uint32_t* s_col = nullptr;
+    double* s_val = nullptr;
+    int64_t s_nnz = 0;
+    int s_state = 0;       // 0: not examined; 1: built; -1: not worth it (too many two-part entries)
 };
 
 // Kernel classes timed by the optional per-launch profiler.
@@ -72,6 +83,9 @@ struct ss_ctx_s {
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
     double* h_pinned = nullptr;      // small pinned host buffer for scalars
+    // limit of every bounded device-side wait (triangular-solve dependencies,
+    // staging barriers), after which the kernel reports SS_ERR_TIMEOUT
+    unsigned long long wait_ns = 2000000000ull;
 };
 
 struct ss_mat_s {
@@ -81,27 +95,39 @@ struct ss_mat_s {
     int64_t d = 0;                    // Hilbert dimension when the matrix is a Liouvillian (n = d^2)
 };
 
-struct TriLevels {                    // level-scheduled triangular factor
+struct TriLevels {                    // one level-scheduled strict triangle of the factors
     int32_t n_levels = 0;
     int32_t* order = nullptr;         // rows sorted by level (device, n)
-    int32_t* units = nullptr;         // level-aligned units of 32/g rows, -1 padded (device)
-    int4* meta = nullptr;             // per unit row: {row, first entry, end of the triangle's part} (device)
-    int64_t n_units = 0;
-    int g = 32;                       // lanes per row in the solve
+    int g = 32;                       // lanes per row in the solve (R = 32 / g rows per unit)
+    int64_t n_units = 0;              // level-aligned units of R rows
+    // The triangle in unit order, stored on its own: slot s = u R + k is the
+    // k-th row of unit u (urow[s] = -1 pads a unit at the end of a level);
+    // its entries are col/val[uptr[s] .. uptr[s + 1]), so a unit's entries
+    // are contiguous.  src maps each entry to its position in the combined
+    // factors (values are gathered from there after every factorisation).
+    int32_t* urow = nullptr;          // n_units R
+    int32_t* uptr = nullptr;          // n_units R + 1
+    int32_t* col = nullptr;           // nnz
+    int32_t* src = nullptr;           // nnz
+    double2* val = nullptr;           // nnz
+    float2* val32 = nullptr;          // nnz (mixed precision)
+    double2* dinv = nullptr;          // upper triangle: 1 / u_ii per slot (0 for padding)
+    float2* dinv32 = nullptr;
+    int64_t nnz = 0;
+    int grid64 = 0, grid32 = 0;       // co-resident blocks of the FP64 / FP32 solve kernels (0: not yet known)
 };
 
 struct ss_prec_s {
     DeviceCSR f;                      // combined factors: strict lower = L (unit), rest = U
     int32_t* diag_pos = nullptr;      // device, n
     double2* inv_diag = nullptr;      // 1 / u_ii (device, n)
-    float2* val32 = nullptr;          // FP32 factors (mixed precision)
-    float2* inv_diag32 = nullptr;
+    bool fp32 = false;                // FP32 copies of the triangles exist
     TriLevels lower, upper;
-    uint32_t* flags = nullptr;        // unused (kept null)
-    unsigned long long* tickets = nullptr;  // [0] lower, [1] upper block tickets
     int* err = nullptr;               // device error word (bounded waits)
     double2* tmp = nullptr;           // intermediate vector of the two solves (PENDING between uses)
     float2* tmp32 = nullptr;
+    int64_t skipped_slot = -1;        // diagnostics: lower-solve slot whose row is not computed (-1: none)
+    int32_t skipped_row = -1;
 };
 
 // ----------------------------------------------------------------- errors
@@ -202,8 +228,16 @@ ss_status prec_apply_dev32(ss_ctx ctx, ss_prec M, const float2* r, float2* z, co
 ss_status prec_from_host(ss_ctx ctx, ss_prec M, int64_t n, const std::vector<int32_t>& rp,
                          const std::vector<int32_t>& col, const std::vector<double>& val);
 ss_status prec_check_error(ss_ctx ctx, ss_prec M);
+// Test aid: the lower solve stops computing `row` (its output keeps the
+// PENDING mark, so the rows depending on it wait until their limit), or with
+// restore != 0 computes it again.
+ss_status prec_skip_row(ss_ctx ctx, ss_prec M, int64_t row, int restore);
 void prec_destroy(ss_ctx ctx, ss_prec M);
 
 // SpMV
 ss_status spmv_dev(ss_ctx ctx, const DeviceCSR& A, const double2* x, double2* y);
 ss_status spmv_dev32(ss_ctx ctx, const DeviceCSR& A, const float2* val32, const float2* x, float2* y);
+// Builds A's part-split copy when it pays (at most 1.6 parts per entry);
+// later FP64 SpMVs of A use it.
+ss_status csr_split(ss_ctx ctx, DeviceCSR& A);
+void csr_split_free(ss_ctx ctx, DeviceCSR& A);

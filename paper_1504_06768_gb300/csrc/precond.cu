@@ -52,8 +52,6 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-constexpr unsigned long long WAIT_NS = 2000000000ull;   // a single wait gives up after 2 s
-
 // "Not yet computed" marks: NaN bit patterns with a payload that arithmetic
 // never produces (arithmetic NaNs carry the canonical payload).
 constexpr unsigned long long PENDING64 = 0xFFFDEADBEEFDEAD1ull;
@@ -73,93 +71,164 @@ template <> __device__ __forceinline__ float2 pending<float2>() {
     return make_float2(__uint_as_float(PENDING32), __uint_as_float(PENDING32));
 }
 
-// Sync-free triangular solve.  One warp handles one "unit": up to R = 32 / G
-// rows of the same level, G lanes per row.  Blocks take consecutive runs of
-// units in level order through a ticket counter (one atomic per block), so a
-// row only ever waits for rows held by earlier, resident blocks.  The output
-// vector starts filled with the PENDING mark; a row waits (bounded) until the
-// values it depends on are no longer PENDING -- the value itself is the
-// completion signal, so no flag or fence is needed.
+// Sync-free triangular solve on a persistent grid.  Each triangle is stored
+// on its own in level order, cut into level-aligned units of R = 32 / G rows
+// (G lanes per row); a unit's entries are contiguous, so a warp reads them
+// as one coalesced run.  Units are dealt to the warps of a co-resident grid
+// round-robin (unit u to warp u mod W, each warp in increasing u), so every
+// dependency of a unit lies in a smaller unit, held by a running warp that
+// waits only on smaller units in turn: the solve always progresses, with no
+// atomics and no ticket.  The output vector starts filled with the PENDING
+// mark; a row waits (bounded) until the values it depends on are no longer
+// PENDING -- the value itself is the completion signal, so no flag or fence
+// is needed.  While a warp waits on its unit, the row records and the first
+// K entries per lane of its next unit, and the row records of the one after,
+// are already on their way: in the steady state a unit costs one dependent
+// round trip (the x values) once its inputs are ready.
 //   LOWER: x_i = b_i - sum_{j<i} l_ij x_j (unit diagonal); also re-marks
 //          `other[i]` (the upper solve's output) PENDING.
 //   UPPER: x_i = (b_i - sum_{j>i} u_ij x_j) / u_ii; afterwards re-marks b_i
 //          (the lower solve's output) PENDING for the next application.
-// A row's range comes from a precomputed record {row, first, end, -} of its
-// unit, and in FP32 each lane issues the column and value loads of its next
-// SYNCFREE_K entries, then their x loads, before it waits on any of them, so a
-// row costs three dependent memory round trips when its inputs are ready.
-constexpr int SYNCFREE_K = 4;
+constexpr int TRSV_THREADS = 256;
+constexpr int TRSV_K = 2;      // entries per lane whose loads are issued together
 
-template <bool LOWER, int G, class T>
-__global__ void __launch_bounds__(256) sptrsv_syncfree(const int32_t* __restrict__ col, const T* __restrict__ val,
-                                                       const T* __restrict__ inv_diag, const int4* __restrict__ meta,
-                                                       int64_t n_units, T* b, T* x, T* other,
-                                                       unsigned long long* __restrict__ ticket, int* __restrict__ err,
-                                                       const int* __restrict__ halt) {
+template <class T>
+struct TrsvArgs {
+    const int32_t* urow;
+    const int32_t* uptr;
+    const int32_t* col;
+    const T* val;
+    const T* dinv;             // upper: 1 / u_ii per slot
+    int64_t n_units;
+    const T* b;
+    T* x;
+    T* other;                  // lower: the upper solve's output (re-marked); upper: the lower's (b)
+    int* err;
+    const int* halt;
+    unsigned long long wait_ns;
+};
+
+template <int G, int K, class T>
+struct UnitPf {                // one lane's share of a unit, prefetched
+    int32_t i, s, e;           // row (-1: padding), entry range
+    int32_t c[K];
+    T v[K];
+    T bv, dv;                  // b_i and 1 / u_ii (lane sub == 0)
+};
+
+template <bool LOWER, int G, int K, class T>
+__device__ __forceinline__ void unit_rows(const TrsvArgs<T>& a, int64_t u, int grp, int32_t& i, int32_t& s,
+                                          int32_t& e) {
+    constexpr int R = 32 / G;
+    i = -1;
+    s = e = 0;
+    if (u < a.n_units) {
+        const int64_t slot = u * R + grp;
+        i = __ldg(&a.urow[slot]);
+        s = __ldg(&a.uptr[slot]);
+        e = __ldg(&a.uptr[slot + 1]);
+    }
+}
+
+template <bool LOWER, int G, int K, class T>
+__device__ __forceinline__ void unit_entries(const TrsvArgs<T>& a, int64_t u, int grp, int sub,
+                                             UnitPf<G, K, T>& p) {
     using C = Cplx<T>;
     constexpr int R = 32 / G;
-    constexpr int K = sizeof(T) == 16 ? 1 : SYNCFREE_K;   // FP64: registers of more in-flight entries cost more
-    if (halt && *halt) return;      // uniform over the launch: no ticket is taken
-    __shared__ unsigned long long s_ticket;
-    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1ull);
-    __syncthreads();
-    const int64_t nblocks = gridDim.x;
-    const int64_t wpb = blockDim.x >> 5;
-    const int64_t u = (int64_t)(s_ticket % (unsigned long long)nblocks) * wpb + (threadIdx.x >> 5);
-    if (u >= n_units) return;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const int32_t k = p.s + sub + q * G;
+        p.c[q] = k < p.e ? __ldcs(&a.col[k]) : -1;
+        p.v[q] = k < p.e ? __ldcs(&a.val[k]) : C::zero();
+    }
+    p.bv = C::zero();
+    p.dv = C::zero();
+    if (p.i >= 0 && sub == 0) {
+        p.bv = __ldcg(&a.b[p.i]);
+        if (!LOWER) p.dv = __ldg(&a.dinv[u * R + grp]);
+    }
+}
+
+// x[c], waiting (bounded) while it is PENDING; 0 after a timeout.
+template <class T>
+__device__ __forceinline__ T wait_ready(const TrsvArgs<T>& a, int32_t c, T v, bool& timed_out) {
+    if (ready(v)) return v;
+    const T* xp = &a.x[c];
+    const unsigned long long t0 = globaltimer_ns();
+    int spins = 0;
+    while (true) {
+        if (++spins > 8) __nanosleep(spins > 64 ? 256 : 32);
+        v = __ldcv(xp);
+        if (ready(v)) return v;
+        if ((spins & 15) == 0 && (*(volatile int*)a.err != 0 || globaltimer_ns() - t0 > a.wait_ns)) {
+            // raised at once, so that every other wait of the launch gives up at its next check
+            if (*(volatile int*)a.err == 0) atomicExch(a.err, 1);
+            timed_out = true;
+            return Cplx<T>::zero();
+        }
+    }
+}
+
+template <bool LOWER, int G, int K, class T>
+__global__ void __launch_bounds__(TRSV_THREADS) sptrsv_syncfree(TrsvArgs<T> a) {
+    using C = Cplx<T>;
+    if (a.halt && *a.halt) return;      // uniform over the launch
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane % G;
-    const int4 m = meta[u * R + grp];              // row -1 pads a unit at the end of a level
-    const int32_t i = m.x, s = m.y, e = m.z;
-    T dinv = C::zero();
-    if (!LOWER && i >= 0 && sub == 0) dinv = inv_diag[i];
-    T acc = C::zero();
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+    int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (u >= a.n_units) return;
     bool timed_out = false;
-    for (int32_t base = s + sub; base < e; base += K * G) {
-        int32_t c[K];
-        T v[K], xj[K];
+    UnitPf<G, K, T> cur, nxt;
+    unit_rows<LOWER, G, K, T>(a, u, grp, cur.i, cur.s, cur.e);
+    unit_rows<LOWER, G, K, T>(a, u + W, grp, nxt.i, nxt.s, nxt.e);
+    unit_entries<LOWER, G, K, T>(a, u, grp, sub, cur);
+    for (; u < a.n_units; u += W) {
+        // requests for the next two units go out before this unit's wait
+        int32_t i2, s2, e2;
+        unit_rows<LOWER, G, K, T>(a, u + 2 * W, grp, i2, s2, e2);
+        unit_entries<LOWER, G, K, T>(a, u + W, grp, sub, nxt);
+        T xj[K];
 #pragma unroll
-        for (int q = 0; q < K; ++q) {
-            const int32_t k = base + q * G;
-            c[q] = k < e ? col[k] : -1;
-            v[q] = k < e ? val[k] : C::zero();
-        }
+        for (int q = 0; q < K; ++q) xj[q] = cur.c[q] >= 0 ? __ldcv(&a.x[cur.c[q]]) : C::zero();
+        T acc = C::zero();
 #pragma unroll
-        for (int q = 0; q < K; ++q) xj[q] = c[q] >= 0 ? __ldcv(&x[c[q]]) : C::zero();
+        for (int q = 0; q < K; ++q)
+            if (cur.c[q] >= 0) acc = C::fma_(cur.v[q], wait_ready(a, cur.c[q], xj[q], timed_out), acc);
+        // entries beyond the first K G of a long row
+        for (int32_t base = cur.s + sub + K * G; base < cur.e; base += K * G) {
+            int32_t c[K];
+            T v[K], xv[K];
 #pragma unroll
-        for (int q = 0; q < K; ++q) {
-            if (c[q] >= 0 && !ready(xj[q])) {
-                const T* xp = &x[c[q]];
-                const unsigned long long t0 = globaltimer_ns();
-                int spins = 0;
-                while (true) {
-                    if (++spins > 64) __nanosleep(64);
-                    xj[q] = __ldcv(xp);
-                    if (ready(xj[q])) break;
-                    if ((spins & 63) == 0 && (*(volatile int*)err != 0 || globaltimer_ns() - t0 > WAIT_NS)) {
-                        timed_out = true;
-                        xj[q] = C::zero();
-                        break;
-                    }
-                }
+            for (int q = 0; q < K; ++q) {
+                const int32_t k = base + q * G;
+                c[q] = k < cur.e ? __ldcs(&a.col[k]) : -1;
+                v[q] = k < cur.e ? __ldcs(&a.val[k]) : C::zero();
             }
-            acc = C::fma_(v[q], xj[q], acc);
-        }
-    }
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-        T other_v = C::shfl_down(acc, o);
-        acc.x += other_v.x;
-        acc.y += other_v.y;
+            for (int q = 0; q < K; ++q) xv[q] = c[q] >= 0 ? __ldcv(&a.x[c[q]]) : C::zero();
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+                if (c[q] >= 0) acc = C::fma_(v[q], wait_ready(a, c[q], xv[q], timed_out), acc);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            T ov = C::shfl_down(acc, o);
+            acc.x += ov.x;
+            acc.y += ov.y;
+        }
+        if (cur.i >= 0 && sub == 0) {
+            T xi = C::sub(cur.bv, acc);
+            if (!LOWER) xi = C::mul(xi, cur.dv);
+            __stcg(&a.x[cur.i], xi);
+            if (a.other) __stcg(&a.other[cur.i], pending<T>());
+        }
+        cur = nxt;
+        nxt.i = i2;
+        nxt.s = s2;
+        nxt.e = e2;
     }
-    if (__any_sync(FULL, timed_out) && lane == 0) atomicExch(err, 1);
-    if (i >= 0 && sub == 0) {
-        T xi = C::sub(b[i], acc);
-        if (!LOWER) xi = C::mul(xi, dinv);
-        __stcg(&x[i], xi);
-        if (LOWER) __stcg(&other[i], pending<T>());
-        else __stcg(&b[i], pending<T>());
-    }
+    if (__any_sync(FULL, timed_out) && lane == 0) atomicExch(a.err, 1);
 }
 
 template <class T>
@@ -236,36 +305,117 @@ __global__ void check_missing_diag(const int32_t* __restrict__ dpos, int64_t n, 
     if (i < n && dpos[i] < 0) atomicExch(err, 2);
 }
 
-ss_status upload_levels(ss_ctx ctx, const std::vector<int32_t>& order, const std::vector<int32_t>& lptr,
-                        double avg_row, TriLevels& L, int32_t nlev, bool lower, const std::vector<int32_t>& hrp,
-                        const std::vector<int32_t>& hdpos) {
-    L.n_levels = nlev;
+// Lanes per row of a triangle: enough that K entries per lane cover a row of
+// the triangle's mean length, at least 2 (G divides 32).
+int trsv_lanes(double avg_row) {
     int g = 2;
-    while (g < 32 && g < avg_row) g <<= 1;
-    L.g = g;
-    std::vector<int32_t> units;
-    level_units_host(order, lptr, 32 / g, units);
-    L.n_units = (int64_t)units.size() / (32 / g);
-    // per unit row: {row, first entry, end} of the triangle's part of the row
-    std::vector<int4> meta(units.size());
-    for (size_t k = 0; k < units.size(); ++k) {
-        const int32_t i = units[k];
-        if (i < 0) meta[k] = make_int4(-1, 0, 0, 0);
-        else if (hdpos[i] < 0) meta[k] = make_int4(i, 0, 0, 0);     // no diagonal: reported as a zero pivot
-        else if (lower) meta[k] = make_int4(i, hrp[i], hdpos[i], 0);
-        else meta[k] = make_int4(i, hdpos[i] + 1, hrp[i + 1], 0);
+    while (g < 32 && g * TRSV_K < avg_row) g <<= 1;
+    return g;
+}
+
+// One strict triangle (lower: columns < i, upper: columns > i) of the
+// combined factors in unit order: level-aligned units of R rows, each unit's
+// entries contiguous.  Only the pattern is needed here; values are gathered
+// after the numeric factorisation (pack_triangle).
+ss_status build_triangle(ss_ctx ctx, const std::vector<int32_t>& order, const std::vector<int32_t>& lptr,
+                         int32_t nlev, bool lower, const std::vector<int32_t>& hrp, const std::vector<int32_t>& hcol,
+                         TriLevels& T) {
+    const int64_t n = (int64_t)hrp.size() - 1;
+    T.n_levels = nlev;
+    int64_t nnz_t = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t t = hrp[i]; t < hrp[i + 1]; ++t) nnz_t += lower ? hcol[t] < i : hcol[t] > i;
+    T.g = trsv_lanes(n ? (double)nnz_t / n : 1.0);
+    const int R = 32 / T.g;
+    std::vector<int32_t> urow;
+    level_units_host(order, lptr, R, urow);
+    T.n_units = (int64_t)urow.size() / R;
+    T.nnz = nnz_t;
+    std::vector<int32_t> uptr(urow.size() + 1), tcol((size_t)nnz_t), tsrc((size_t)nnz_t);
+    int64_t k = 0;
+    for (size_t sl = 0; sl < urow.size(); ++sl) {
+        uptr[sl] = (int32_t)k;
+        const int32_t i = urow[sl];
+        if (i < 0) continue;
+        for (int32_t t = hrp[i]; t < hrp[i + 1]; ++t)
+            if (lower ? hcol[t] < i : hcol[t] > i) {
+                tcol[k] = hcol[t];
+                tsrc[k] = t;
+                ++k;
+            }
     }
-    SS_TRY(dev_alloc_n(ctx, &L.meta, meta.size()));
-    SS_CUDA(ctx, cudaMemcpyAsync(L.meta, meta.data(), sizeof(int4) * meta.size(), cudaMemcpyHostToDevice,
+    uptr[urow.size()] = (int32_t)k;
+    SS_TRY(dev_alloc_n(ctx, &T.order, order.size()));
+    SS_TRY(dev_alloc_n(ctx, &T.urow, urow.size()));
+    SS_TRY(dev_alloc_n(ctx, &T.uptr, uptr.size()));
+    SS_TRY(dev_alloc_n(ctx, &T.col, tcol.size()));
+    SS_TRY(dev_alloc_n(ctx, &T.src, tsrc.size()));
+    SS_CUDA(ctx, cudaMemcpyAsync(T.order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice,
                                  ctx->stream));
-    SS_TRY(dev_alloc_n(ctx, &L.order, order.size()));
-    SS_TRY(dev_alloc_n(ctx, &L.units, units.size()));
-    SS_CUDA(ctx, cudaMemcpyAsync(L.order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice,
+    SS_CUDA(ctx, cudaMemcpyAsync(T.urow, urow.data(), sizeof(int32_t) * urow.size(), cudaMemcpyHostToDevice,
                                  ctx->stream));
-    SS_CUDA(ctx, cudaMemcpyAsync(L.units, units.data(), sizeof(int32_t) * units.size(), cudaMemcpyHostToDevice,
+    SS_CUDA(ctx, cudaMemcpyAsync(T.uptr, uptr.data(), sizeof(int32_t) * uptr.size(), cudaMemcpyHostToDevice,
                                  ctx->stream));
-    SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (nnz_t) {
+        SS_CUDA(ctx, cudaMemcpyAsync(T.col, tcol.data(), sizeof(int32_t) * tcol.size(), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+        SS_CUDA(ctx, cudaMemcpyAsync(T.src, tsrc.data(), sizeof(int32_t) * tsrc.size(), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+    }
+    SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));     // the host vectors go out of scope
     return SS_OK;
+}
+
+__global__ void gather_values(const double2* __restrict__ f, const int32_t* __restrict__ src, int64_t nnz,
+                              double2* __restrict__ v, float2* __restrict__ v32) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+        const double2 a = f[src[k]];
+        v[k] = a;
+        if (v32) v32[k] = make_float2((float)a.x, (float)a.y);
+    }
+}
+
+__global__ void gather_dinv(const double2* __restrict__ inv, const int32_t* __restrict__ urow, int64_t slots,
+                            double2* __restrict__ d, float2* __restrict__ d32) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < slots; s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = urow[s];
+        const double2 a = i >= 0 ? inv[i] : make_double2(0.0, 0.0);
+        d[s] = a;
+        if (d32) d32[s] = make_float2((float)a.x, (float)a.y);
+    }
+}
+
+// Values of one triangle in unit order (FP64, and FP32 when asked), and for
+// the upper triangle 1 / u_ii per slot, from the combined factors.
+ss_status pack_triangle(ss_ctx ctx, ss_prec M, TriLevels& T, bool upper, bool fp32) {
+    const int64_t slots = T.n_units * (32 / T.g);
+    if (!T.val) SS_TRY(dev_alloc_n(ctx, &T.val, (size_t)T.nnz));
+    if (fp32 && !T.val32) SS_TRY(dev_alloc_n(ctx, &T.val32, (size_t)T.nnz));
+    if (T.nnz)
+        gather_values<<<(ss_count_launch(), std::min<unsigned>(grid_for(T.nnz, 256), 4096)), 256, 0, ctx->stream>>>(
+            M->f.val, T.src, T.nnz, T.val, fp32 ? T.val32 : nullptr);
+    if (upper) {
+        if (!T.dinv) SS_TRY(dev_alloc_n(ctx, &T.dinv, (size_t)slots));
+        if (fp32 && !T.dinv32) SS_TRY(dev_alloc_n(ctx, &T.dinv32, (size_t)slots));
+        if (slots)
+            gather_dinv<<<(ss_count_launch(), std::min<unsigned>(grid_for(slots, 256), 4096)), 256, 0, ctx->stream>>>(
+                M->inv_diag, T.urow, slots, T.dinv, fp32 ? T.dinv32 : nullptr);
+    }
+    SS_CUDA(ctx, cudaGetLastError());
+    return SS_OK;
+}
+
+void free_triangle(ss_ctx ctx, TriLevels& T) {
+    dev_free(ctx, T.order);
+    dev_free(ctx, T.urow);
+    dev_free(ctx, T.uptr);
+    dev_free(ctx, T.col);
+    dev_free(ctx, T.src);
+    dev_free(ctx, T.val);
+    dev_free(ctx, T.val32);
+    dev_free(ctx, T.dinv);
+    dev_free(ctx, T.dinv32);
+    T = TriLevels();
 }
 
 }  // namespace
@@ -277,21 +427,11 @@ static ss_status analyse(ss_ctx ctx, ss_prec M, const std::vector<int32_t>& hrp,
     std::vector<int32_t> upper_order, upper_ptr;
     int32_t nl = level_sets_host(n, hrp.data(), hcol.data(), true, lower_order, lower_ptr);
     int32_t nu = level_sets_host(n, hrp.data(), hcol.data(), false, upper_order, upper_ptr);
-    int64_t nnz_lower = 0;
-    for (int64_t i = 0; i < n; ++i)
-        for (int32_t t = hrp[i]; t < hrp[i + 1] && hcol[t] < i; ++t) ++nnz_lower;
-    const int64_t nnz_upper = (int64_t)hcol.size() - nnz_lower - n;
-    std::vector<int32_t> hdpos(n, -1);
-    for (int64_t i = 0; i < n; ++i)
-        for (int32_t t = hrp[i]; t < hrp[i + 1]; ++t)
-            if (hcol[t] == i) { hdpos[i] = t; break; }
-    SS_TRY(upload_levels(ctx, lower_order, lower_ptr, n ? (double)nnz_lower / n : 1.0, M->lower, nl, true, hrp, hdpos));
-    SS_TRY(upload_levels(ctx, upper_order, upper_ptr, n ? (double)nnz_upper / n : 1.0, M->upper, nu, false, hrp, hdpos));
-    SS_TRY(dev_alloc_n(ctx, &M->tickets, 2));
+    SS_TRY(build_triangle(ctx, lower_order, lower_ptr, nl, true, hrp, hcol, M->lower));
+    SS_TRY(build_triangle(ctx, upper_order, upper_ptr, nu, false, hrp, hcol, M->upper));
     SS_TRY(dev_alloc_n(ctx, &M->err, 1));
     SS_TRY(dev_alloc_n(ctx, &M->tmp, (size_t)n));
     fill_pending<double2><<<(ss_count_launch(), 256), 256, 0, ctx->stream>>>(n, M->tmp);
-    SS_CUDA(ctx, cudaMemsetAsync(M->tickets, 0, sizeof(unsigned long long) * 2, ctx->stream));
     SS_CUDA(ctx, cudaMemsetAsync(M->err, 0, sizeof(int), ctx->stream));
     return SS_OK;
 }
@@ -350,15 +490,14 @@ ss_status prec_finish(ss_ctx ctx, ss_prec M, bool want_fp32) {
     const int64_t n = M->f.n_rows;
     SS_TRY(dev_alloc_n(ctx, &M->inv_diag, (size_t)n));
     if (want_fp32) {
-        SS_TRY(dev_alloc_n(ctx, &M->val32, (size_t)M->f.nnz));
-        SS_TRY(dev_alloc_n(ctx, &M->inv_diag32, (size_t)n));
         SS_TRY(dev_alloc_n(ctx, &M->tmp32, (size_t)n));
         fill_pending<float2><<<(ss_count_launch(), 256), 256, 0, ctx->stream>>>(n, M->tmp32);
     }
-    make_inv_diag<<<(ss_count_launch(), grid_for(n, 256)), 256, 0, ctx->stream>>>(M->f.val, M->diag_pos, n, M->inv_diag, M->inv_diag32,
-                                                             M->err);
-    if (want_fp32 && M->f.nnz > 0)
-        to_f32<<<(ss_count_launch(), grid_for(M->f.nnz, 256)), 256, 0, ctx->stream>>>(M->f.val, M->f.nnz, M->val32);
+    make_inv_diag<<<(ss_count_launch(), grid_for(n, 256)), 256, 0, ctx->stream>>>(M->f.val, M->diag_pos, n,
+                                                                                    M->inv_diag, nullptr, M->err);
+    M->fp32 = want_fp32;
+    SS_TRY(pack_triangle(ctx, M, M->lower, false, want_fp32));
+    SS_TRY(pack_triangle(ctx, M, M->upper, true, want_fp32));
     SS_CUDA(ctx, cudaGetLastError());
     int herr = 0;
     SS_CUDA(ctx, cudaMemcpyAsync(&herr, M->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -368,62 +507,97 @@ ss_status prec_finish(ss_ctx ctx, ss_prec M, bool want_fp32) {
     return SS_OK;
 }
 
-template <bool LOWER, class T>
-static void launch_trsv(ss_ctx ctx, ss_prec M, const TriLevels& L, const T* vals, const T* inv, T* b, T* x, T* other,
-                        unsigned long long* ticket, const int* halt) {
-    const int threads = 256;
-    const unsigned g = (unsigned)((L.n_units * 32 + threads - 1) / threads);
-#define SS_TRSV_CASE(GG)                                                                                    \
-    case GG:                                                                                                \
-        sptrsv_syncfree<LOWER, GG, T><<<(ss_count_launch(), g), threads, 0, ctx->stream>>>(M->f.col, vals, inv, L.meta,  \
-                                                                       L.n_units, b, x, other, ticket,       \
-                                                                       M->err, halt);                        \
-        break;
-    switch (L.g) {
-        SS_TRSV_CASE(2)
-        SS_TRSV_CASE(4)
-        SS_TRSV_CASE(8)
-        SS_TRSV_CASE(16)
-        default:
-        SS_TRSV_CASE(32)
+// Launches one triangular solve on a co-resident grid (a cooperative launch,
+// so that every warp whose unit another waits on is running).
+template <bool LOWER, int G, class T>
+static ss_status launch_trsv_g(ss_ctx ctx, const TriLevels& L, int& grid_cache, TrsvArgs<T> a) {
+    auto kern = sptrsv_syncfree<LOWER, G, TRSV_K, T>;
+    constexpr int wpb = TRSV_THREADS / 32;
+    if (grid_cache == 0) {
+        int per_sm = 0;
+        SS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TRSV_THREADS, 0));
+        if (per_sm < 1) return set_error(ctx, SS_ERR_CUDA, "triangular solve kernel cannot be resident");
+        grid_cache = per_sm * std::max(ctx->num_sms, 1);
     }
-#undef SS_TRSV_CASE
+    const int64_t need = (L.n_units + wpb - 1) / wpb;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, grid_cache));
+    void* args[] = {&a};
+    ss_count_launch();
+    SS_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(TRSV_THREADS), args, 0,
+                                             ctx->stream));
+    return SS_OK;
+}
+
+template <bool LOWER, class T>
+static ss_status launch_trsv(ss_ctx ctx, ss_prec M, TriLevels& L, const T* vals, const T* dinv, const T* b, T* x,
+                             T* other, const int* halt) {
+    TrsvArgs<T> a;
+    a.urow = L.urow;
+    a.uptr = L.uptr;
+    a.col = L.col;
+    a.val = vals;
+    a.dinv = dinv;
+    a.n_units = L.n_units;
+    a.b = b;
+    a.x = x;
+    a.other = other;
+    a.err = M->err;
+    a.halt = halt;
+    a.wait_ns = ctx->wait_ns;
+    int& gc = sizeof(T) == 16 ? L.grid64 : L.grid32;
+    switch (L.g) {
+        case 2: return launch_trsv_g<LOWER, 2, T>(ctx, L, gc, a);
+        case 4: return launch_trsv_g<LOWER, 4, T>(ctx, L, gc, a);
+        case 8: return launch_trsv_g<LOWER, 8, T>(ctx, L, gc, a);
+        case 16: return launch_trsv_g<LOWER, 16, T>(ctx, L, gc, a);
+        default: return launch_trsv_g<LOWER, 32, T>(ctx, L, gc, a);
+    }
 }
 
 // z = U^{-1} L^{-1} r.  tmp (the lower solve's output) is all PENDING between
 // applications; the lower solve marks z PENDING and the upper solve restores
 // tmp.  r and z must not alias.
 template <class T>
-static ss_status apply_impl(ss_ctx ctx, ss_prec M, const T* vals, const T* inv, T* tmp, const T* r, T* z,
+static ss_status apply_impl(ss_ctx ctx, ss_prec M, const T* lv, const T* uv, const T* ud, T* tmp, const T* r, T* z,
                             const int* halt) {
     const int64_t n = M->f.n_rows;
     if (n == 0) return SS_OK;
     {
         ProfScope ps(ctx, PROF_TRSV_LOWER);
-        launch_trsv<true, T>(ctx, M, M->lower, vals, inv, const_cast<T*>(r), tmp, z, M->tickets, halt);
+        SS_TRY((launch_trsv<true, T>(ctx, M, M->lower, lv, nullptr, r, tmp, z, halt)));
     }
     {
         ProfScope ps(ctx, PROF_TRSV_UPPER);
-        launch_trsv<false, T>(ctx, M, M->upper, vals, inv, tmp, z, nullptr, M->tickets + 1, halt);
+        SS_TRY((launch_trsv<false, T>(ctx, M, M->upper, uv, ud, tmp, z, tmp, halt)));
     }
     SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;
 }
 
 ss_status prec_apply_dev(ss_ctx ctx, ss_prec M, const double2* r, double2* z, const int* halt) {
-    return apply_impl<double2>(ctx, M, M->f.val, M->inv_diag, M->tmp, r, z, halt);
+    return apply_impl<double2>(ctx, M, M->lower.val, M->upper.val, M->upper.dinv, M->tmp, r, z, halt);
 }
 
 ss_status prec_apply_dev32(ss_ctx ctx, ss_prec M, const float2* r, float2* z, const int* halt) {
-    if (!M->val32) return set_error(ctx, SS_ERR_INVALID, "preconditioner has no FP32 factors");
-    return apply_impl<float2>(ctx, M, M->val32, M->inv_diag32, M->tmp32, r, z, halt);
+    if (!M->fp32) return set_error(ctx, SS_ERR_INVALID, "preconditioner has no FP32 factors");
+    return apply_impl<float2>(ctx, M, M->lower.val32, M->upper.val32, M->upper.dinv32, M->tmp32, r, z, halt);
 }
 
+// After a wait gave up, the intermediate vectors no longer hold the PENDING
+// mark everywhere: they are re-marked (and the error word cleared) so that
+// the next application starts from the invariant again.
 ss_status prec_check_error(ss_ctx ctx, ss_prec M) {
     int herr = 0;
     SS_CUDA(ctx, cudaMemcpyAsync(&herr, M->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (herr == 1) return set_error(ctx, SS_ERR_TIMEOUT, "triangular solve wait timed out");
+    if (herr == 1) {
+        const int64_t n = M->f.n_rows;
+        fill_pending<double2><<<(ss_count_launch(), 256), 256, 0, ctx->stream>>>(n, M->tmp);
+        if (M->tmp32) fill_pending<float2><<<(ss_count_launch(), 256), 256, 0, ctx->stream>>>(n, M->tmp32);
+        SS_CUDA(ctx, cudaMemsetAsync(M->err, 0, sizeof(int), ctx->stream));
+        SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        return set_error(ctx, SS_ERR_TIMEOUT, "triangular solve wait timed out");
+    }
     return SS_OK;
 }
 
@@ -431,17 +605,38 @@ void prec_destroy(ss_ctx ctx, ss_prec M) {
     free_csr(ctx, M->f);
     dev_free(ctx, M->diag_pos);
     dev_free(ctx, M->inv_diag);
-    dev_free(ctx, M->val32);
-    dev_free(ctx, M->inv_diag32);
-    dev_free(ctx, M->lower.order);
-    dev_free(ctx, M->upper.order);
-    dev_free(ctx, M->lower.units);
-    dev_free(ctx, M->upper.units);
-    dev_free(ctx, M->lower.meta);
-    dev_free(ctx, M->upper.meta);
-    dev_free(ctx, M->flags);
-    dev_free(ctx, M->tickets);
+    free_triangle(ctx, M->lower);
+    free_triangle(ctx, M->upper);
     dev_free(ctx, M->err);
     dev_free(ctx, M->tmp);
     dev_free(ctx, M->tmp32);
+}
+
+// ------------------------------------------------------------ diagnostics
+
+ss_status prec_skip_row(ss_ctx ctx, ss_prec M, int64_t row, int restore) {
+    TriLevels& T = M->lower;
+    const int64_t slots = T.n_units * (32 / T.g);
+    if (restore) {
+        if (M->skipped_slot < 0) return SS_OK;
+        SS_CUDA(ctx, cudaMemcpyAsync(T.urow + M->skipped_slot, &M->skipped_row, sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, ctx->stream));
+        SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        M->skipped_slot = -1;
+        return SS_OK;
+    }
+    if (M->skipped_slot >= 0) return set_error(ctx, SS_ERR_INVALID, "a row is already skipped");
+    std::vector<int32_t> urow((size_t)slots);
+    SS_CUDA(ctx, cudaMemcpyAsync(urow.data(), T.urow, sizeof(int32_t) * slots, cudaMemcpyDeviceToHost, ctx->stream));
+    SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int64_t sl = 0; sl < slots; ++sl)
+        if (urow[sl] == row) {
+            const int32_t none = -1;
+            SS_CUDA(ctx, cudaMemcpyAsync(T.urow + sl, &none, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+            SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            M->skipped_slot = sl;
+            M->skipped_row = (int32_t)row;
+            return SS_OK;
+        }
+    return set_error(ctx, SS_ERR_INVALID, "row out of range");
 }

@@ -81,6 +81,7 @@ struct ss_server_s {
     ss_server_options so{};
     size_t budget = 0, in_use = 0;
     PatternCache cache;
+    SolutionCache sols;                  // warm starts (so.warm_start)
     std::vector<Slot> slots;
     std::unique_ptr<ss_ctx_s> large_ctx;
     std::mutex mu;
@@ -166,6 +167,7 @@ void fast_lane(ss_server s) {
         w.rho_on_device = 0;
         w.stage_pinned = true;
         w.cache = &s->cache;
+        w.sols = s->so.warm_start ? &s->sols : nullptr;
         for (auto& r : take) {
             w.H.push_back(&r->H.view);
             w.n_c.push_back((int)r->cviews.size());
@@ -249,6 +251,7 @@ extern "C" void ss_server_options_default(ss_server_options* so) {
     so->hbm_budget_mb = 0.0;
     so->max_waves = 4;
     so->max_wave_systems = 0;
+    so->warm_start = 0;
 }
 
 extern "C" ss_status ss_server_create(int device, const ss_options* opt, const ss_server_options* so_in,
@@ -266,6 +269,7 @@ extern "C" ss_status ss_server_create(int device, const ss_options* opt, const s
     s->device = device;
     ss_options_default(&s->opt);
     if (opt) s->opt = *opt;
+    s->opt.warm_start = 0;          // a request's output buffer carries no initial guess
     ss_server_options_default(&s->so);
     if (so_in) s->so = *so_in;
     int sms = 1;
@@ -299,6 +303,9 @@ extern "C" ss_status ss_server_destroy(ss_server s) {
     if (s->worker.joinable()) s->worker.join();
     if (s->large_worker.joinable()) s->large_worker.join();
     cudaSetDevice(s->device);
+    if (!s->slots.empty() && s->slots[0].ctx) {
+        s->sols.clear(s->slots[0].ctx.get());       // stream-ordered frees on a slot stream, synchronised below
+    }
     for (Slot& sl : s->slots) {
         if (sl.ctx && sl.ctx->stream) {
             cudaStreamSynchronize(sl.ctx->stream);

@@ -121,6 +121,29 @@ __global__ void unpermute_normalise(int64_t n, const int32_t* __restrict__ perm,
         rho[perm[r]] = cdiv(x[r], tr);
 }
 
+// tr(rho) of a natural-order column-major rho (one block, fixed order)
+__global__ void natural_trace(int64_t d, const double2* __restrict__ rho, double2* __restrict__ out) {
+    __shared__ double2 sh[256];
+    double2 s = make_double2(0.0, 0.0);
+    for (int64_t i = threadIdx.x; i < d; i += blockDim.x) s = cadd(s, rho[i * (d + 1)]);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] = cadd(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+// x[r] = rho[perm[r]] / tr (the warm start), or 0 when tr = 0
+__global__ void permute_scaled(int64_t n, const int32_t* __restrict__ perm, const double2* __restrict__ rho,
+                               const double2* __restrict__ trace, double2* __restrict__ x) {
+    const double2 tr = *trace;
+    const bool use = tr.x != 0.0 || tr.y != 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        x[r] = use ? cdiv(rho[perm[r]], tr) : make_double2(0.0, 0.0);
+}
+
 __global__ void max_abs_partial(int64_t n, const double2* __restrict__ x, double* __restrict__ part) {
     __shared__ double sh[256];
     double s = 0.0;
@@ -248,6 +271,14 @@ ss_status su_lrho(ss_ctx ctx, const DeviceCSR& A, const double2* x, int mode, do
     double trm = hypot(tr.x, tr.y);
     *out = trm > 0.0 ? sqrt(h) / trm : INFINITY;
     if (trace_host) *trace_host = tr;
+    return SS_OK;
+}
+
+ss_status su_warm_start(ss_ctx ctx, int64_t n, int64_t d, const int32_t* perm_dev, const double2* rho_dev,
+                        double2* trace_dev, double2* x) {
+    natural_trace<<<(ss_count_launch(), 1), 256, 0, ctx->stream>>>(d, rho_dev, trace_dev);
+    permute_scaled<<<(ss_count_launch(), 1024), 256, 0, ctx->stream>>>(n, perm_dev, rho_dev, trace_dev, x);
+    SS_CUDA(ctx, cudaGetLastError());
     return SS_OK;
 }
 

@@ -66,6 +66,55 @@ __global__ void __launch_bounds__(256) spmv_kernel(const int32_t* __restrict__ r
     if (row < n && sub == 0) y[row] = acc;
 }
 
+// y = A x from the part-split copy of A (FP64): a part is one real value v
+// and a column word c (bit 31: the value is an imaginary part i v).  A real
+// part adds (v x.re, v x.im), an imaginary one (-v x.im, v x.re): two FMAs
+// against one x load, the operands picked by selects and the sign by a bit
+// flip, so the FP64 pipe only sees the FMAs and the lane reduction.
+template <int G, int K>
+__global__ void __launch_bounds__(256) spmv_split_kernel(const int32_t* __restrict__ rp,
+                                                         const uint32_t* __restrict__ col,
+                                                         const double* __restrict__ val, int64_t n,
+                                                         const double2* __restrict__ x, double2* __restrict__ y,
+                                                         const int* __restrict__ halt) {
+    if (halt && *halt) return;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = gid / G;
+    const int sub = threadIdx.x % G;
+    double2 acc = make_double2(0.0, 0.0);
+    if (row < n) {
+        const int32_t a = rp[row], b = rp[row + 1];
+        for (int32_t base = a + sub; base < b; base += K * G) {
+            uint32_t c[K];
+            double v[K];
+            double2 xv[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int32_t t = base + k * G;
+                c[k] = t < b ? __ldcs(&col[t]) : 0u;
+                v[k] = t < b ? __ldcs(&val[t]) : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) xv[k] = __ldg(&x[c[k] & 0x7fffffffu]);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const bool im = (c[k] >> 31) != 0u;
+                const double pr = im ? xv[k].y : xv[k].x;      // multiplies v into re(y)
+                const double pi = im ? xv[k].x : xv[k].y;      // and into im(y)
+                const double vr = __longlong_as_double(__double_as_longlong(v[k]) ^ ((long long)im << 63));
+                acc.x = fma(vr, pr, acc.x);
+                acc.y = fma(v[k], pi, acc.y);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+    }
+    if (row < n && sub == 0) y[row] = acc;
+}
+
 // Lanes per row for a mean row length (FP64: the FP64 pipe is the scarce unit,
 // fewer lanes per row; FP32: more lanes, more loads in flight).
 int spmv_group_size(int64_t n_rows, int64_t nnz, bool fp32);

@@ -42,6 +42,7 @@ void free_csr(ss_ctx ctx, DeviceCSR& m) {
     dev_free(ctx, m.row_ptr);
     dev_free(ctx, m.col);
     dev_free(ctx, m.val);
+    csr_split_free(ctx, m);
     m = DeviceCSR();
 }
 

@@ -65,11 +65,11 @@ def test_options_defaults(lib):
     import ctypes
     from paper_1504_06768_gb300 import _binding as B
     o = B.Options()
-    o.lgmres_k, o.inner_rtol = 77, 9.0            # the last fields: written at the offsets the header gives
+    o.lgmres_k, o.inner_rtol, o.warm_start = 77, 9.0, 5   # the last fields: written at the offsets the header gives
     lib.ss_options_default(ctypes.byref(o))
     assert (o.method, o.precond, o.precision, o.maxiter, o.restart, o.use_rcm) == (2, 0, 0, 1000, 30, 1)
     assert o.tol == 1e-10 and o.sigma == 1e-15 and o.drop_tol == 1e-4 and o.fill_factor == 10.0
-    assert o.inner_rtol == 1e-5 and o.lgmres_k == 0
+    assert o.inner_rtol == 1e-5 and o.lgmres_k == 0 and o.warm_start == 0
     assert B.METHODS["auto"] == 4 and B.METHOD_NAMES[B.METHODS["iterative-lgmres"]] == "iterative-lgmres"
 
 

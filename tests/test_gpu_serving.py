@@ -102,3 +102,26 @@ def test_wait_timeout_leaves_request_queryable(ss):
             srv.wait(t, timeout_s=0.0)
         rho, info, lat = srv.wait(t, timeout_s=300)
         assert info["status"] == 0 and lat > 0
+
+
+def test_served_sweep_warm_starts_from_earlier_requests(ss):
+    """With warm_start, a request starts from the stored state of the closest
+    earlier request with the same pattern: a drive sweep served point after
+    point reaches the same states (against the cold server and the oracle)
+    in fewer iterations, and a repeated request needs almost none."""
+    sweep = [jaynes_cummings_rwa(N=12, E=0.5 + 0.02 * k) for k in range(8)]
+
+    def serve(warm):
+        out = []
+        with ss.Server(precision="mixed", tol=1e-10, warm_start=warm) as srv:
+            for s in sweep + sweep[3:4]:                   # the last request repeats an earlier one
+                out.append(srv.wait(srv.submit(s.H, s.c_ops), timeout_s=120))
+        return out
+
+    cold, warm = serve(False), serve(True)
+    for s, (rc, ic, _), (rw, iw, _) in zip(sweep + sweep[3:4], cold, warm):
+        assert ic["status"] == 0 and iw["status"] == 0 and iw["resid_Lrho"] <= 1e-10
+        assert trace_distance(rc, rw) <= 1e-8
+    assert trace_distance(warm[5][0], steady_state_dense(sweep[5].H, sweep[5].c_ops)) <= 1e-8
+    assert sum(i["iters"] for _, i, _ in warm[1:8]) < sum(i["iters"] for _, i, _ in cold[1:8])
+    assert warm[8][1]["iters"] <= 2 < cold[8][1]["iters"]
