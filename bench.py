@@ -377,6 +377,24 @@ def run_gpu(args):
                   "ms_setup_mean": statistics.mean(i["ms_setup"] for i in step_infos),
                   "ms_solve_mean": statistics.mean(i["ms_solve"] for i in step_infos)},
     }
+    if rank == 0 and not args.no_configs:
+        # the same step with the autotuned launch choices (tuned once, then kept by the context)
+        opt.autotune = 1
+        step()
+        infos.clear()
+        tt = timed(max(1, min(args.steps, 3)))
+        tinf = list(infos)
+        infos.clear()
+        opt.autotune = 0
+        tms = sum(tt) / len(tt)
+        out["autotune"] = {"choice": {"lanes_shift_lower_upper_A": tinf[0]["tune_lanes_shift"],
+                                      "stage_flip": tinf[0]["tune_stage"]},
+                           "value_tuned": BATCH / (tms / 1000.0), "ms_per_step_tuned": tms,
+                           "value_rule": value, "precision": args.precision,
+                           "max_resid_Lrho": max(i["resid_Lrho"] for i in tinf)}
+    if rank == 0 and not args.no_configs:
+        out["sweep_warm_start"] = sweep_warm_measure(B, lib, ctx, stream, opt, systems, dev_inputs, rho_dev,
+                                                     step_infos, rho_main)
     if rank == 0 and not args.no_spmv:
         out["spmv"] = spmv_measure(ss, B, ctx, stream)
     if rank == 0 and not args.no_serve:
@@ -391,6 +409,63 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return out if rank == 0 else None
+
+
+def sweep_warm_measure(B, lib, ctx, stream, opt, systems, dev_inputs, rho_dev, cold_infos, cold_rho):
+    """The benchmark's drive sweep solved as a warm-started sweep: the systems
+    in order of their drive E, every fourth one solved cold, then the rest in
+    one more launch, each starting from the steady state of the nearest
+    solved point (steady_state_batched with warm_start; the guesses are
+    copied into the output buffers on the device, inside the timed region).
+    Compared with the cold step's solves/s and iterations."""
+    import ctypes as C
+    import numpy as np
+    import torch
+    k_all = sorted(range(len(systems)), key=lambda k: systems[k].params["E"])
+    first = k_all[::4]
+    rest = [k for k in k_all if k not in set(first)]
+    pos = {k: i for i, k in enumerate(k_all)}
+    # nearest pass-1 point (in E order) for every other point
+    src = [first[min(range(len(first)), key=lambda j: abs(pos[first[j]] - pos[k]))] for k in rest]
+
+    def call(idx, warm):
+        nb = len(idx)
+        Hs = (B.CsrView * nb)(*[dev_inputs[k][0] for k in idx])
+        ncs = (C.c_int * nb)(*[dev_inputs[k][2] for k in idx])
+        cp = (C.POINTER(B.CsrView) * nb)(*[C.cast(dev_inputs[k][1], C.POINTER(B.CsrView)) for k in idx])
+        outs = (C.c_void_p * nb)(*[rho_dev[k].data_ptr() for k in idx])
+        inf = (B.Info * nb)()
+        saved = opt.warm_start
+        opt.warm_start = 1 if warm else 0
+        st = lib.steady_state_batched(ctx.handle, nb, Hs, ncs, cp, C.byref(opt), outs, 1, inf)
+        opt.warm_start = saved
+        if st != 0:
+            raise RuntimeError(f"warm sweep: {B.STATUS_NAMES.get(st)} {lib.ss_last_error(ctx.handle).decode()}")
+        return [inf[j].as_dict() for j in range(nb)]
+
+    src_t = torch.as_tensor(src, device="cuda")
+    rest_t = torch.as_tensor(rest, device="cuda")
+    times, i1, i2 = [], None, None
+    for rep in range(3):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        i1 = call(first, False)
+        rho_dev.index_copy_(0, rest_t, rho_dev.index_select(0, src_t))      # the neighbours' states as guesses
+        i2 = call(rest, True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    td = _trace_distances(rho_dev[rest_t].cpu().numpy(), cold_rho[rest], systems[0].d)
+    cold_iters = ({k: cold_infos[k]["iters"] for k in range(len(systems))}     # the first timed step, cold
+                  if len(cold_infos) >= len(systems) else {})
+    return {"systems": len(systems), "cold_first_pass": len(first), "warm_second_pass": len(rest),
+            "solves_per_s": len(systems) / (ms / 1000.0), "ms": ms,
+            "iters_mean_warm_pass": statistics.mean(i["iters"] for i in i2),
+            "iters_mean_cold_same_systems": (statistics.mean(cold_iters[k] for k in rest) if cold_iters else None),
+            "converged": sum(i["status"] == 0 for i in i1 + i2),
+            "trace_distance_warm_vs_cold": {"max": float(td.max()), "median": float(np.median(td))}}
 
 
 # ------------------------------------------------ SpMV roofline and serving
@@ -441,9 +516,10 @@ def _time_spmv(ss, B, ctx, stream, Ap, reps):
                      "peak_source": kind}
     # complex CSR bytes above (20 nnz + 36 n); the split form moves 12 bytes
     # per part and does 2 FP64 FMAs per part (GB300: about 1.26 TFLOP/s FP64)
-    sb = parts * 12 + (n + 1) * 4 + 2 * n * 16
+    sb = parts * 12 + (n + 1) * 4 + n * 4 + 2 * n * 16
     us = res["fp64"]["us"]
-    res["fp64"].update({"format": "part-split (value + column word per nonzero real/imaginary part)",
+    res["fp64"].update({"format": "part-split (value + column per nonzero real or imaginary part; per row the "
+                                  "real parts, then the imaginary ones)",
                         "parts": parts, "bytes_split": sb, "GB/s_split": sb / (us * 1e-6) / 1e9,
                         "frac_hbm_split": sb / (us * 1e-6) / 1e9 / peak,
                         "fp64_tflops": 4.0 * parts / (us * 1e-6) / 1e12})
@@ -569,18 +645,21 @@ def configs_measure(ss):
     k4 = {"systems": len(kerr), "n_range": [min(s.d for s in kerr) ** 2, max(s.d for s in kerr) ** 2],
           "tol": TOL}
     rb = {}
-    for prec in ("mixed", "fp64"):
-        ss.steady_state_batched(pairs[:8], tol=TOL, precision=prec)          # warm
+    for prec, tune in (("mixed", False), ("mixed", True), ("fp64", False)):
+        ss.steady_state_batched(pairs if tune else pairs[:8], tol=TOL, precision=prec, autotune=tune)   # warm
         times = []
         for _ in range(3):
             t0 = time.perf_counter()
-            rhos, infos = ss.steady_state_batched(pairs, tol=TOL, precision=prec, raise_on_failure=False)
+            rhos, infos = ss.steady_state_batched(pairs, tol=TOL, precision=prec, raise_on_failure=False,
+                                                  autotune=tune)
             times.append(time.perf_counter() - t0)
-        rb[prec] = rhos
-        k4[f"batched_{prec}"] = {"solves_per_s": len(kerr) / statistics.median(times),
-                                 "s_per_call": statistics.median(times),
-                                 "converged": sum(i["status"] == 0 and i["resid_Lrho"] <= TOL for i in infos),
-                                 "iters_mean": statistics.mean(i["iters"] for i in infos)}
+        if not tune:
+            rb[prec] = rhos
+        k4[f"batched_{prec}" + ("_autotuned" if tune else "")] = {
+            "solves_per_s": len(kerr) / statistics.median(times), "s_per_call": statistics.median(times),
+            "converged": sum(i["status"] == 0 and i["resid_Lrho"] <= TOL for i in infos),
+            "iters_mean": statistics.mean(i["iters"] for i in infos),
+            **({"choice": [infos[0]["tune_lanes_shift"], infos[0]["tune_stage"]]} if tune else {})}
     t0 = time.perf_counter()
     single, sinfo = [], []
     for H, cs in pairs:
@@ -652,7 +731,7 @@ def serve_sweep(ss, args):
                 picks = rng.integers(0, 1 << 30, size=n_req)
                 t0 = time.perf_counter()
                 due = t0
-                tickets = []
+                tickets, subs = [], []
                 for k in range(n_req):
                     due += gaps[k]
                     delay = due - time.perf_counter()
@@ -664,20 +743,25 @@ def serve_sweep(ss, args):
                         sysm, cls = pool_jc[picks[k] % len(pool_jc)], "jc40"
                     else:
                         sysm, cls = pool_kerr[picks[k] % len(pool_kerr)], "kerr"
+                    subs.append(time.perf_counter())
                     tickets.append((srv.submit(sysm.H, sysm.c_ops), cls))
-                lat, ok, by = [], 0, {}
-                for t, cls in tickets:
+                lat, ok, by, done_at = [], 0, {}, {}
+                for (t, cls), t_sub in zip(tickets, subs):
                     _, info, ms = srv.wait(t, timeout_s=600, raise_on_failure=False)
                     lat.append(ms)
                     good = info["status"] == 0 and info["resid_Lrho"] <= TOL
                     ok += good
                     by.setdefault(cls, []).append(ms)
+                    done_at.setdefault(cls, []).append(t_sub + ms / 1000.0)
                 wall = time.perf_counter() - t0
                 lat = np.array(lat)
                 out["runs"].append({"precision": prec, "rate_per_s": rate, "requests": n_req,
                                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                                     "solves_per_s": n_req / wall, "converged": int(ok),
-                                    "p50_ms_by_class": {c: float(np.percentile(v, 50)) for c, v in by.items()}})
+                                    "by_class": {c: {"requests": len(v), "p50_ms": float(np.percentile(v, 50)),
+                                                     "p99_ms": float(np.percentile(v, 99)),
+                                                     "solves_per_s": len(v) / max(max(done_at[c]) - t0, 1e-9)}
+                                                 for c, v in by.items()}})
     return out
 
 

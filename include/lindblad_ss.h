@@ -111,6 +111,12 @@ typedef struct {
                               neighbouring point of a parameter sweep, say): the Krylov iteration
                               starts from it, scaled to unit trace (inverse power: the start
                               vector).  A guess of zero trace falls back to the zero start.  0   */
+    int autotune;          /* steady_state_batched: 1 = choose the persistent solver's lanes per row
+                              (of the two triangles and of L~) and its level staging by timing short
+                              capped runs of candidate choices on the batch's first systems
+                              (coordinate descent from the rule-based choice); the choice is kept per
+                              context for batches of the same shape.  Results are those of the chosen
+                              launch, to the same tolerance.  0: the rules                         */
 } ss_options;
 
 /* Per-solve diagnostics. */
@@ -128,6 +134,9 @@ typedef struct {
     double ms_setup, ms_solve;           /* wall time of setup and of the iteration      */
     int method;            /* ss_method that ran (the choice of SS_METHOD_AUTO)        */
     int64_t bw_modified, bw_shifted;     /* SS_METHOD_AUTO: RCM bandwidths compared; else 0 */
+    int32_t tune_lanes_shift[3];         /* batched solver: lanes per row of the lower triangle, the
+                                            upper triangle and L~ as log2 multiples of the rule's choice */
+    int32_t tune_stage;                  /* 1: the level staging other than the rule's (see autotune)  */
 } ss_info;
 
 /* ---------------------------------------------------------------- context */
@@ -427,6 +436,16 @@ ss_status ss_profile_read(ss_ctx ctx, int kind, int64_t* launches, double* total
 /* Number of CUDA kernels this library has launched in the process so far
  * (all contexts). */
 unsigned long long ss_launch_count(void);
+/* The autotuner's search on a table of costs instead of measured runs (a
+ * test of its logic; needs no GPU): cost_table[((l*4 + u)*4 + a)*2 + s] is the
+ * cost of lanes-per-row shifts (l-1, u-1, a-1) and staging flag s.  Starting
+ * from (0, 0, 0, 0), coordinate descent moves to a neighbour while the cost
+ * drops by more than 1 %, evaluating each choice at most once and at most
+ * max_probes choices.  best_out (4 values) receives the choice, *probes_out
+ * (may be NULL) the evaluations made. */
+ss_status ss_tune_search_host(const double* cost_table, int32_t max_probes, int32_t* best_out,
+                              int32_t* probes_out);
+
 /* Limit of every bounded device-side wait issued through this context: a
  * triangular solve waiting for a row it depends on, a staging barrier of the
  * batched solver.  Default 2 s; a wait that reaches it makes the call return
@@ -439,6 +458,15 @@ ss_status ss_set_wait_limit(ss_ctx ctx, uint64_t limit_ns);
  * precond_apply returns SS_ERR_TIMEOUT); restore != 0 undoes it.
  * SS_ERR_INVALID for a row outside M or a second skipped row. */
 ss_status ss_diag_prec_skip_row(ss_ctx ctx, ss_prec M, int64_t row, int restore);
+
+/* Failure-detection aid, not part of the paper's method: in later
+ * steady_state_batched calls on this context whose triangular solves stage
+ * their levels through the shared-memory ring (the FP64 form), every block's
+ * staging number `seq` (counted from 0 over the levels it stages) arms its
+ * barrier without issuing the copies, so the solving warps wait until the
+ * wait limit, and the call reports SS_ERR_TIMEOUT for the systems of that
+ * launch.  seq = -1 (the default) turns it off.  SS_ERR_INVALID below -1. */
+ss_status ss_diag_batched_stall(ss_ctx ctx, int64_t seq);
 
 /* Number of device and pinned-host memory allocations this library has made
  * in the process so far (all contexts): a call that allocates nothing leaves

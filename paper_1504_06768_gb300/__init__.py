@@ -126,6 +126,18 @@ def mbm_host(A):
     return match, matched.value
 
 
+def tune_search_host(cost_table, max_probes: int = 64):
+    """The batched solver's autotuner search on a table of costs (no GPU):
+    cost_table has shape (4, 4, 4, 2) over the lanes-per-row shifts -1..2 of
+    the lower triangle, the upper triangle and L~, and the staging flag.
+    Returns (best choice (lo, up, a, stage), number of evaluations)."""
+    t = np.ascontiguousarray(np.asarray(cost_table, dtype=np.float64).reshape(4, 4, 4, 2))
+    best = (C.c_int32 * 4)()
+    probes = C.c_int32()
+    _host_status(B.load().ss_tune_search_host(t.ctypes.data, max_probes, best, C.byref(probes)), "ss_tune_search_host")
+    return tuple(best), probes.value
+
+
 def level_sets_host(A, lower: bool = True):
     """Level sets of the strict lower (or upper) triangle of A's pattern on
     the host: (order, level_ptr)."""
@@ -388,7 +400,7 @@ def krylov_solve(A: Matrix, M: Preconditioner, b, x0=None, method: str = "bicgst
 
 
 def _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed,
-             inner_rtol=1e-5, lgmres_k=0, warm_start=0):
+             inner_rtol=1e-5, lgmres_k=0, warm_start=0, autotune=0):
     opt = B.Options()
     B.load().ss_options_default(C.byref(opt))
     opt.method = B.METHODS[method]
@@ -400,6 +412,7 @@ def _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_f
     opt.inner_rtol = inner_rtol
     opt.lgmres_k = lgmres_k
     opt.warm_start = int(bool(warm_start))
+    opt.autotune = int(bool(autotune))
     return opt
 
 
@@ -408,7 +421,7 @@ def steady_state_batched(systems: Sequence, method: str = "iterative-bicgstab", 
                          drop_tol: float = 1e-4, fill_factor: float = 10.0, w: float = 0.0, sigma: float = 1e-15,
                          use_rcm: bool = True, seed: int = 0, ctx: Optional[Context] = None,
                          raise_on_failure: bool = True, inner_rtol: float = 1e-5, lgmres_k: int = 0,
-                         rho_init: Optional[Sequence] = None):
+                         rho_init: Optional[Sequence] = None, autotune: bool = False):
     """Steady states of many systems, each given as (H, c_ops); returns a list
     of rho (numpy, d x d) and a list of info dicts.  rho_init: optional
     initial guesses (one d x d matrix per system, e.g. the steady states of
@@ -427,7 +440,7 @@ def steady_state_batched(systems: Sequence, method: str = "iterative-bicgstab", 
     outs = (C.c_void_p * max(ns, 1))(*[r.ctypes.data for r in rhos])
     infos = (B.Info * max(ns, 1))()
     opt = _options(method, tol, precond, precision, maxiter, restart, drop_tol, fill_factor, w, sigma, use_rcm, seed,
-                   inner_rtol, lgmres_k, rho_init is not None)
+                   inner_rtol, lgmres_k, rho_init is not None, autotune)
     st = B.load().steady_state_batched(ctx.handle, ns, Hs, ncs, cptrs, C.byref(opt), outs, 0, infos)
     if st != 0 and (raise_on_failure or st not in (B.SS_NOT_CONVERGED, B.SS_BREAKDOWN)):
         ctx.check(st, "steady_state_batched")

@@ -35,7 +35,7 @@ class Options(C.Structure):
                 ("maxiter", C.c_int), ("restart", C.c_int), ("drop_tol", C.c_double),
                 ("fill_factor", C.c_double), ("w", C.c_double), ("sigma", C.c_double),
                 ("use_rcm", C.c_int), ("seed", C.c_uint64), ("inner_rtol", C.c_double), ("lgmres_k", C.c_int),
-                ("warm_start", C.c_int)]
+                ("warm_start", C.c_int), ("autotune", C.c_int)]
 
 
 class Info(C.Structure):
@@ -44,10 +44,12 @@ class Info(C.Structure):
                 ("n", C.c_int64), ("nnz", C.c_int64), ("bandwidth", C.c_int64), ("profile", C.c_int64),
                 ("nnz_factors", C.c_int64), ("levels_lower", C.c_int32), ("levels_upper", C.c_int32),
                 ("ms_setup", C.c_double), ("ms_solve", C.c_double), ("method", C.c_int),
-                ("bw_modified", C.c_int64), ("bw_shifted", C.c_int64)]
+                ("bw_modified", C.c_int64), ("bw_shifted", C.c_int64),
+                ("tune_lanes_shift", C.c_int32 * 3), ("tune_stage", C.c_int32)]
 
     def as_dict(self) -> dict:
         out = {k: getattr(self, k) for k, _ in self._fields_}
+        out["tune_lanes_shift"] = list(self.tune_lanes_shift)
         out["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
         out["method_name"] = METHOD_NAMES.get(self.method, str(self.method))
         return out
@@ -100,7 +102,9 @@ _SIGNATURES = {
     "ss_launch_count": (C.c_ulonglong, []),
     "ss_alloc_count": (C.c_ulonglong, []),
     "ss_set_wait_limit": (C.c_int, [_P, C.c_uint64]),
+    "ss_tune_search_host": (C.c_int, [_P, C.c_int32, _P, C.POINTER(C.c_int32)]),
     "ss_diag_prec_skip_row": (C.c_int, [_P, _P, C.c_int64, C.c_int]),
+    "ss_diag_batched_stall": (C.c_int, [_P, C.c_int64]),
     "lgmres_solve": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int, C.c_int, C.c_int,
                                C.POINTER(C.c_int), _DP]),
     "ss_rcm_order_host": (C.c_int, [C.c_int64, _P, _P, _P]),

@@ -150,6 +150,7 @@ extern "C" void ss_options_default(ss_options* o) {
     o->inner_rtol = 1e-5;
     o->lgmres_k = 0;
     o->warm_start = 0;
+    o->autotune = 0;
 }
 
 // ----------------------------------------------------------------- matrices
@@ -305,6 +306,7 @@ extern "C" void ss_mat_free(ss_mat A) {
     dev_free_nostream(A->diag_pos);
     dev_free_nostream(A->val32);
     dev_free_nostream(A->m.s_row_ptr);
+    dev_free_nostream(A->m.s_mid);
     dev_free_nostream(A->m.s_col);
     dev_free_nostream(A->m.s_val);
     cudaStreamSynchronize(0);
@@ -387,6 +389,12 @@ extern "C" ss_status precond_apply_f32(ss_ctx ctx, ss_prec M, const float* r, fl
 extern "C" ss_status ss_set_wait_limit(ss_ctx ctx, uint64_t limit_ns) {
     if (!ctx || limit_ns == 0) return SS_ERR_INVALID;
     ctx->wait_ns = limit_ns;
+    return SS_OK;
+}
+
+extern "C" ss_status ss_diag_batched_stall(ss_ctx ctx, int64_t seq) {
+    if (!ctx || seq < -1) return SS_ERR_INVALID;
+    ctx->diag_stall_seq = seq;
     return SS_OK;
 }
 

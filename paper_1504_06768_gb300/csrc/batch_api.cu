@@ -99,7 +99,14 @@ ss_status upload_vec(ss_ctx ctx, const std::vector<T>& h, T** d) {
 // factorization"), the permuted pattern with the gather map of its values,
 // the level sets of the two triangles and the packed operands.  Runs on any
 // host thread; touches nothing on the device.
-void build_pattern_host(Pattern& P, int use_rcm) {
+// Lanes per row scaled by 2^shift (the autotuner's choice), within 1..32.
+int shifted_lanes(int g, int shift) {
+    while (shift > 0 && g < 32) { g <<= 1; --shift; }
+    while (shift < 0 && g > 1) { g >>= 1; ++shift; }
+    return g;
+}
+
+void build_pattern_host(Pattern& P, int use_rcm, const TuneChoice& tune) {
     const int64_t n = (int64_t)P.rp.size() - 1, d = P.d;
     P.perm.resize(n);
     if (use_rcm) rcm_host(n, P.rp.data(), P.col.data(), P.perm.data());
@@ -151,13 +158,13 @@ void build_pattern_host(Pattern& P, int use_rcm) {
             llen[r] = P.dpos[r] - prp[r];
             ulen[r] = prp[r + 1] - P.dpos[r] - 1;
         }
-        P.lo_g = lanes_for_triangle(std::move(llen));
-        P.up_g = lanes_for_triangle(std::move(ulen));
+        P.lo_g = shifted_lanes(lanes_for_triangle(std::move(llen)), tune.lo);
+        P.up_g = shifted_lanes(lanes_for_triangle(std::move(ulen)), tune.up);
     }
     {
         std::vector<int32_t> alen(n);
         for (int64_t r = 0; r < n; ++r) alen[r] = prp[r + 1] - prp[r];
-        P.a_g = lanes_for_triangle(std::move(alen));
+        P.a_g = shifted_lanes(lanes_for_triangle(std::move(alen)), tune.a);
     }
     level_units_host(P.lorder, P.lptr, 32 / P.lo_g, P.lunits);
     level_units_host(uorder, uptr, 32 / P.up_g, P.uunits);
@@ -346,6 +353,11 @@ void wave_release(BatchWave& w) {
         cudaEventDestroy(w.done);
         w.done = nullptr;
     }
+    for (cudaEvent_t* e : {&w.k0, &w.k1})
+        if (*e) {
+            cudaEventDestroy(*e);
+            *e = nullptr;
+        }
     w.launched = false;
 }
 
@@ -421,12 +433,12 @@ ss_status wave_begin(BatchWave& w) {
         SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         const size_t nth = std::max<size_t>(1, std::min<size_t>(fresh.size(), std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()))));
         if (nth <= 1) {
-            for (size_t p : fresh) build_pattern_host(*w.pats[p], opt.use_rcm);
+            for (size_t p : fresh) build_pattern_host(*w.pats[p], opt.use_rcm, w.tune);
         } else {
             std::vector<std::thread> th;
             for (size_t t = 0; t < nth; ++t)
                 th.emplace_back([&, t]() {
-                    for (size_t k = t; k < fresh.size(); k += nth) build_pattern_host(*w.pats[fresh[k]], opt.use_rcm);
+                    for (size_t k = t; k < fresh.size(); k += nth) build_pattern_host(*w.pats[fresh[k]], opt.use_rcm, w.tune);
                 });
             for (auto& x : th) x.join();
         }
@@ -571,7 +583,16 @@ ss_status wave_begin(BatchWave& w) {
             for (size_t l = 0; l + 1 < lv->size(); ++l) wide = std::max(wide, (*lv)[l + 1] - (*lv)[l]);
         shapes[q] = BatchShape{(int32_t)blt.n[q], P.lo.nlev, P.up.nlev, P.lo.E, 32 / P.lo.G, P.up.E, 32 / P.up.G, wide};
     }
+    bp.stage_flip = w.tune.stage;
+    bp.wait_ns = ctx->wait_ns;
+    bp.diag_stall_seq = ctx->diag_stall_seq;
+    if (w.time_kernel) {
+        if (!w.k0) SS_CUDA(ctx, cudaEventCreate(&w.k0));
+        if (!w.k1) SS_CUDA(ctx, cudaEventCreate(&w.k1));
+        SS_CUDA(ctx, cudaEventRecord(w.k0, ctx->stream));
+    }
     WSTEP(batch_launch(ctx, w.dsys, (int)ns, bp, shapes, w.ctl, w.ctl + 1));
+    if (w.time_kernel) SS_CUDA(ctx, cudaEventRecord(w.k1, ctx->stream));
     if (w.stage_pinned) {
         // results to pinned memory, asynchronously: [descriptors][error word][rho ...]
         const size_t hs_bytes = (ns * sizeof(BatchSys) + 255) & ~size_t(255);
@@ -625,6 +646,7 @@ ss_status wave_end(BatchWave& w, ss_info* infos) {
         return cuda_check(ctx, e, "steady_state_batched");
     }
     w.t2 = now_ms();
+    if (w.time_kernel && w.k0 && w.k1) cudaEventElapsedTime(&w.kernel_ms, w.k0, w.k1);
     if (w.sols && !herr) {
         for (size_t q = 0; q < ns; ++q)
             if (w.hs[q].status == SS_OK) {
@@ -653,6 +675,10 @@ ss_status wave_end(BatchWave& w, ss_info* infos) {
             inf.levels_upper = P.up_levels;
             inf.ms_setup = (w.t1 - w.t0) / ns;
             inf.ms_solve = (w.t2 - w.t1) / ns;
+            inf.tune_lanes_shift[0] = w.tune.lo;
+            inf.tune_lanes_shift[1] = w.tune.up;
+            inf.tune_lanes_shift[2] = w.tune.a;
+            inf.tune_stage = w.tune.stage;
         }
         if (w.hs[q].status != SS_OK) {
             if (w.hs[q].status != SS_NOT_CONVERGED && w.hs[q].status != SS_BREAKDOWN) worst = (ss_status)w.hs[q].status;
@@ -666,6 +692,101 @@ ss_status wave_end(BatchWave& w, ss_info* infos) {
 
 extern "C" ss_status steady_state(ss_ctx, const ss_csr_view*, int, const ss_csr_view*, const ss_options*, double*, int,
                                   ss_info*);
+
+namespace {
+
+// One probe of the autotuner: the batch's first systems (up to one per SM)
+// with a capped iteration count under the candidate choice; the cost is the
+// persistent kernel's device time per system-iteration.
+struct TuneProbe {
+    ss_ctx ctx;
+    ss_options opt;
+    std::vector<const ss_csr_view*> H, C;
+    std::vector<int> n_c;
+    std::vector<double*> rho;             // device scratch, one per system
+};
+
+double probe_cost(const TuneChoice& c, void* user) {
+    TuneProbe& t = *static_cast<TuneProbe*>(user);
+    BatchWave w;
+    w.ctx = t.ctx;
+    w.opt = t.opt;
+    w.rho_on_device = 1;
+    w.H = t.H;
+    w.C = t.C;
+    w.n_c = t.n_c;
+    w.rho_out = t.rho;
+    w.tune = c;
+    w.time_kernel = true;
+    if (wave_begin(w) != SS_OK) return INFINITY;
+    std::vector<ss_info> inf(t.H.size());
+    const ss_status st = wave_end(w, inf.data());
+    if (st != SS_OK && st != SS_NOT_CONVERGED && st != SS_BREAKDOWN) return INFINITY;
+    double iters = 0.0;
+    for (const ss_info& i : inf) iters += i.iters;
+    return iters > 0.0 ? (double)w.kernel_ms / iters : INFINITY;
+}
+
+// Shape of a batch for the tuning table: precision, and per system the
+// dimension and the operators' entry counts (FNV-1a).
+unsigned long long batch_shape_key(const ss_options& opt, const std::vector<const ss_csr_view*>& H,
+                                   const std::vector<int>& n_c, const std::vector<const ss_csr_view*>& C) {
+    unsigned long long h = 1469598103934665603ull;
+    auto mix = [&](long long v) {
+        for (int b = 0; b < 8; ++b) {
+            h ^= (unsigned long long)((v >> (8 * b)) & 0xff);
+            h *= 1099511628211ull;
+        }
+    };
+    mix(opt.precision);
+    for (size_t k = 0; k < H.size(); ++k) {
+        mix(H[k]->n_rows);
+        mix(H[k]->nnz);
+        mix(n_c[k]);
+        for (int c = 0; c < n_c[k]; ++c) mix(C[k][c].nnz);
+    }
+    return h;
+}
+
+// The autotuner (ss_options.autotune): coordinate descent from the rules'
+// choice over probes of the batch's first systems; the result is kept in the
+// context's table for batches of the same shape.
+ss_status autotune_batch(ss_ctx ctx, const BatchWave& w, TuneChoice* out) {
+    const unsigned long long key = batch_shape_key(w.opt, w.H, w.n_c, w.C);
+    auto it = ctx->tune_table.find(key);
+    if (it != ctx->tune_table.end()) {
+        *out = TuneChoice{it->second[0], it->second[1], it->second[2], it->second[3]};
+        return SS_OK;
+    }
+    TuneProbe t;
+    t.ctx = ctx;
+    t.opt = w.opt;
+    t.opt.maxiter = 8;
+    t.opt.warm_start = 0;
+    t.opt.autotune = 0;
+    const size_t k = std::min<size_t>(w.H.size(), (size_t)std::max(1, ctx->num_sms));
+    size_t total = 0;
+    for (size_t q = 0; q < k; ++q) total += (size_t)w.H[q]->n_rows * w.H[q]->n_rows;
+    double2* scratch = nullptr;
+    SS_TRY(dev_alloc_n(ctx, &scratch, total));
+    size_t off = 0;
+    for (size_t q = 0; q < k; ++q) {
+        t.H.push_back(w.H[q]);
+        t.C.push_back(w.C[q]);
+        t.n_c.push_back(w.n_c[q]);
+        t.rho.push_back(reinterpret_cast<double*>(scratch + off));
+        off += (size_t)w.H[q]->n_rows * w.H[q]->n_rows;
+    }
+    TuneChoice best{0, 0, 0, 0};
+    tune_search(TuneChoice{0, 0, 0, 0}, probe_cost, &t, 10, &best, nullptr);
+    dev_free(ctx, scratch);
+    SS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->tune_table[key] = {best.lo, best.up, best.a, best.stage};
+    *out = best;
+    return SS_OK;
+}
+
+}  // namespace
 
 extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_view* H, const int* n_c,
                                           const ss_csr_view* const* c_ops, const ss_options* opt_in,
@@ -707,6 +828,7 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
         w.C.push_back(n_c[k] ? c_ops[k] : nullptr);
         w.rho_out.push_back(rho_out[k]);
     }
+    if (opt.autotune) SS_TRY(autotune_batch(ctx, w, &w.tune));
     SS_TRY(wave_begin(w));
     std::vector<ss_info> winf(fastidx.size());
     ss_status st = wave_end(w, winf.data());

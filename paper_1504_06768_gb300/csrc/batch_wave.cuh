@@ -17,6 +17,7 @@
 
 #include "batched.cuh"
 #include "common.cuh"
+#include "host_algos.h"
 
 struct PackedDev {                        // device arrays of one packed operand (per pattern)
     int32_t *col = nullptr, *src = nullptr, *lvl = nullptr;
@@ -102,6 +103,9 @@ struct BatchWave {
     bool stage_pinned = false;            // host results: copy through pinned memory, asynchronously
     PatternCache* cache = nullptr;
     SolutionCache* sols = nullptr;        // serving: warm starts from earlier requests (null: off)
+    TuneChoice tune{0, 0, 0, 0};          // lanes-per-row shifts and staging flip (autotuner; 0: the rules)
+    bool time_kernel = false;             // record the persistent kernel's device time (kernel_ms)
+    float kernel_ms = 0.f;
     // state
     BatchLt blt;
     std::vector<std::shared_ptr<Pattern>> pats;
@@ -115,6 +119,7 @@ struct BatchWave {
     double2* stage = nullptr;             // caller-owned pinned buffer of wave_pinned_bytes (stage_pinned)
     std::vector<size_t> stage_off;
     cudaEvent_t done = nullptr;
+    cudaEvent_t k0 = nullptr, k1 = nullptr;   // around the persistent kernel (time_kernel)
     double t0 = 0, t1 = 0, t2 = 0;
     bool launched = false;
 };

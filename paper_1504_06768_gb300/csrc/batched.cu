@@ -193,11 +193,15 @@ struct Ring {
     uint64_t* bars;                 // nslots "full" mbarriers: the slot's copies have landed (shared)
     uint64_t* empty;                // nslots "empty" mbarriers: the slot's level has been solved (shared)
     int* abort;                     // shared flag: a wait ran out of time
+    uint32_t* issued;               // shared: staging sequence numbers issued so far (copies requested)
     int* err;                       // global error word
     int32_t slot_bytes;
     int32_t umax;                   // units per staged level (0: no ring)
     int32_t nslots;                 // slots (2 .. RING_MAX)
     uint32_t seq;                   // levels staged so far by this block
+    uint64_t wait_ns;               // limit of every wait on the ring's barriers
+    int64_t stall_seq;              // failure-detection aid: the staging of this sequence number arms its
+                                    // barrier without issuing the copies (-1: never)
 };
 
 struct SlotLayout {
@@ -255,9 +259,8 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
-constexpr uint64_t RING_WAIT_NS = 2000000000ull;   // 2 s: far beyond any copy; only a fault ends there
-
-// Wait for a phase of one of the ring's mbarriers; after RING_WAIT_NS the
+// Wait for a phase of one of the ring's mbarriers; after rg.wait_ns (2 s by
+// default: far beyond any copy; only a fault or a missing copy ends there) the
 // block gives up, raises the error word and the abort flag, and later waits
 // return at once.
 __device__ __forceinline__ void ring_wait_on(const Ring& rg, uint64_t* bar, unsigned parity) {
@@ -265,7 +268,7 @@ __device__ __forceinline__ void ring_wait_on(const Ring& rg, uint64_t* bar, unsi
     const uint64_t t0 = globaltimer_ns();
     while (!mbar_try_wait(bar, parity)) {
         if (*(volatile int*)rg.abort) return;
-        if (globaltimer_ns() - t0 > RING_WAIT_NS) {
+        if (globaltimer_ns() - t0 > rg.wait_ns) {
             *(volatile int*)rg.abort = 1;
             atomicExch(rg.err, 1);
             return;
@@ -280,7 +283,7 @@ __device__ __forceinline__ void ring_wait(const Ring& rg, int slot, unsigned par
 // One thread: copies of the first min(units, umax) units of level L into slot.
 template <bool LOWER, int G, class T>
 __device__ __forceinline__ void stage_level(const PackedOp& P, const int32_t* lvl, int32_t L, const Ring& rg,
-                                            int slot, const SlotLayout& sl) {
+                                            int slot, const SlotLayout& sl, uint32_t seq) {
     constexpr int R = 32 / G;
     unsigned char* dst = rg.base + (size_t)slot * rg.slot_bytes;
     uint64_t* bar = rg.bars + slot;
@@ -292,7 +295,7 @@ __device__ __forceinline__ void stage_level(const PackedOp& P, const int32_t* lv
     const unsigned bm = (unsigned)(cnt * R * 16);
     const unsigned bd = LOWER ? 0u : (unsigned)(cnt * dinv_stride<T>(R));
     mbar_arrive_tx(bar, bv + bc + bm + bd);
-    if (cnt > 0) {
+    if (cnt > 0 && (int64_t)seq != rg.stall_seq) {
         bulk_g2s(dst, reinterpret_cast<const char*>(P.val) + (size_t)beg * E * 32 * sizeof(T), bv, bar);
         bulk_g2s(dst + sl.col, P.col + (size_t)beg * E * 32, bc, bar);
         bulk_g2s(dst + sl.meta, P.meta + (size_t)beg * R, bm, bar);
@@ -328,7 +331,11 @@ __device__ void cta_trsv_ring(const PackedOp& P, const int32_t* lvl, const int32
                 const uint32_t q = s0 + L;
                 // before its next use, the slot's previous level must be solved
                 if (q >= (uint32_t)ns) ring_wait_on(rg, rg.empty + q % ns, ((q / ns) + 1u) & 1u);
-                stage_level<LOWER, G, T>(P, lvl, L, rg, q % ns, sl);
+                // after an abandoned wait nothing more is staged: a slot whose copies never
+                // came keeps its barrier phase open, and it is not armed a second time
+                if (*(volatile int*)rg.abort) break;
+                stage_level<LOWER, G, T>(P, lvl, L, rg, q % ns, sl, q);
+                *(volatile uint32_t*)rg.issued = q + 1;
             }
         __syncwarp();
     } else {
@@ -380,12 +387,15 @@ __device__ void cta_trsv_ring(const PackedOp& P, const int32_t* lvl, const int32
 // for the copies still in flight into the ring.
 __device__ void ring_drain(const Ring& rg) {
     if (threadIdx.x != 0 || rg.umax == 0 || !*(volatile int*)rg.abort) return;
+    // the last nslots stagings the producer issued (earlier ones were waited for
+    // before their slots were reused)
+    const uint32_t issued = *(volatile uint32_t*)rg.issued;
     for (int k = 1; k <= rg.nslots; ++k) {
-        if (rg.seq < (uint32_t)k) break;
-        const uint32_t q = rg.seq - k;
+        if (issued < (uint32_t)k) break;
+        const uint32_t q = issued - k;
         const uint64_t t0 = globaltimer_ns();
         while (!mbar_try_wait(rg.bars + q % rg.nslots, (q / rg.nslots) & 1u))
-            if (globaltimer_ns() - t0 > RING_WAIT_NS) break;
+            if (globaltimer_ns() - t0 > rg.wait_ns) break;
     }
 }
 
@@ -646,6 +656,7 @@ __device__ KResult cta_bicgstab(Ctx<T>& c, T* x, const T* b, T* wk, double tol, 
         }
         __syncthreads();
         cta_prec<T>(c, p, phat);
+        if (c.ring->umax > 0 && *(volatile int*)c.ring->abort) { res.status = SS_ERR_TIMEOUT; res.iters = it; return res; }
         A dv[3] = {0, 0, 0};
         cta_spmv<T>(S.pa, S.a_col, c.aval, c.buf, v, rhat, dv);
         double dvs[3];
@@ -880,7 +891,8 @@ __device__ void solve_fp64(BatchSys& S, const BatchParams& P, SmemPlan& sm, doub
         double2 tr;
         lr = cta_lrho(S, x, red, &tr);
         if (lr <= P.tol) { status = SS_OK; break; }
-        if (total >= P.maxiter || kr.status == SS_NOT_CONVERGED || (kr.status == SS_BREAKDOWN && kr.iters == 0)) {
+        if (total >= P.maxiter || kr.status == SS_NOT_CONVERGED || kr.status == SS_ERR_TIMEOUT ||
+            (kr.status == SS_BREAKDOWN && kr.iters == 0)) {
             status = kr.status == SS_OK ? SS_NOT_CONVERGED : kr.status;
             break;
         }
@@ -1013,6 +1025,7 @@ __device__ void solve_mixed(BatchSys& S, const BatchParams& P, SmemPlan& sm, dou
             }
             __syncthreads();
             cta_prec_staged<T>(c, ph);          // p^ = M^{-1} p, kept in ph
+            if (c.ring->umax > 0 && *(volatile int*)c.ring->abort) { status = SS_ERR_TIMEOUT; break; }
             A dv[3] = {0, 0, 0};
             cta_spmv<T>(S.pa, S.a_col, c.aval, c.buf, v, rhat, dv);
             double dvs[3];
@@ -1117,14 +1130,14 @@ __device__ void solve_mixed(BatchSys& S, const BatchParams& P, SmemPlan& sm, dou
             beta = cmul(cdiv(rho_new, rho), cdiv(alpha, omega));
             rho = rho_new;
         }
-        if (status == SS_OK) break;
+        if (status == SS_OK || status == SS_ERR_TIMEOUT) break;
         if (restart) {
             fold();
             if (++restarts > 8) { status = SS_BREAKDOWN; break; }
             continue;
         }
     }
-    if (status != SS_OK) {       // final acceptance test on the last iterate
+    if (status != SS_OK && status != SS_ERR_TIMEOUT) {       // final acceptance test on the last iterate
         fold();
         true_residual(S, x, r64, r, red, &lr);
         if (lr <= P.tol) status = SS_OK;
@@ -1160,12 +1173,14 @@ __global__ void __launch_bounds__(BT, BATCH_BLOCKS_PER_SM) batched_solver(BatchS
     __shared__ __align__(8) uint64_t ring_bars[RING_MAX];
     __shared__ __align__(8) uint64_t ring_empty[RING_MAX];
     __shared__ int ring_abort;
+    __shared__ uint32_t ring_issued;
     if (threadIdx.x == 0) {
         for (int r = 0; r < RING_MAX; ++r) {
             mbar_init(ring_bars + r, 1);
             mbar_init(ring_empty + r, 1);
         }
         ring_abort = 0;
+        ring_issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
@@ -1238,11 +1253,14 @@ __global__ void __launch_bounds__(BT, BATCH_BLOCKS_PER_SM) batched_solver(BatchS
             sm.ring.bars = ring_bars;
             sm.ring.empty = ring_empty;
             sm.ring.abort = &ring_abort;
+            sm.ring.issued = &ring_issued;
             sm.ring.err = err;
             sm.ring.slot_bytes = P.ring_slot_bytes;
             sm.ring.umax = P.ring_umax;
             sm.ring.nslots = P.ring_slots;
             sm.ring.seq = ring_seq;
+            sm.ring.wait_ns = P.wait_ns;
+            sm.ring.stall_seq = P.diag_stall_seq;
         }
         __syncthreads();
         if (MIXED) solve_mixed(S, P, sm, red);
@@ -1310,7 +1328,8 @@ int widest_level(const std::vector<BatchShape>& shapes) {
 // boundaries in shared memory first.
 template <class T>
 size_t choose_plan(const std::vector<BatchShape>& shapes, size_t cap, BatchParams& p) {
-    if (p.mixed)
+    const bool ring_first = p.mixed ? p.stage_flip != 0 : p.stage_flip == 0;
+    if (!ring_first)
         for (int pbuf = 1; pbuf >= 0; --pbuf)
             for (int lvl_smem = 1; lvl_smem >= 0; --lvl_smem) {
                 size_t slot = 0;

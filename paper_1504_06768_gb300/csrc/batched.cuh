@@ -79,6 +79,9 @@ struct BatchParams {
     uint64_t seed;
     int ring_allowed;           // every staged array is 16-byte aligned (bulk copies may be used)
     const int32_t* order;       // device: the k-th system taken is order[k] (null: submission order)
+    int stage_flip;             // 1: the level staging the rule would not choose (ring for FP32, none for FP64)
+    unsigned long long wait_ns; // limit of the staging barriers' waits
+    long long diag_stall_seq;   // failure-detection aid: this staging sequence number gets no copies (-1: none)
     // shared-memory plan of the launch (set by batch_launch)
     int ring_umax;              // units per staged level (0: no ring)
     int ring_slots;             // slots of the ring

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -51,12 +53,13 @@ struct DeviceCSR {          // complex FP64 CSR on the device
     int32_t* col = nullptr;
     double2* val = nullptr;
     // Part-split copy for the FP64 SpMV (built on demand by csr_split): each
-    // stored entry becomes one real "part" per nonzero component, s_col
-    // holding its column with bit 31 set for an imaginary part.  Entries of
+    // stored entry becomes one real "part" per nonzero component; a row holds
+    // its real parts, then (from s_mid[i]) its imaginary parts.  Entries of
     // the Liouvillian are mostly purely real (dissipators) or purely
     // imaginary (the Hamiltonian commutator), so a part costs 12 bytes and
     // 2 FMAs where a complex entry costs 20 bytes and 4 FMAs.
     int32_t* s_row_ptr = nullptr;
+    int32_t* s_mid = nullptr;
     uint32_t* s_col = nullptr;
     double* s_val = nullptr;
     int64_t s_nnz = 0;
@@ -86,6 +89,12 @@ struct ss_ctx_s {
     // limit of every bounded device-side wait (triangular-solve dependencies,
     // staging barriers), after which the kernel reports SS_ERR_TIMEOUT
     unsigned long long wait_ns = 2000000000ull;
+    // failure-detection aid (ss_diag_batched_stall): the batched solver's level
+    // staging of this sequence number arms its barrier but issues no copies
+    long long diag_stall_seq = -1;
+    // the batched solver's autotuned choices (lanes-per-row shifts, staging
+    // flip) per batch shape, kept for later batches of the same shape
+    std::map<unsigned long long, std::array<int, 4>> tune_table;
 };
 
 struct ss_mat_s {
@@ -114,7 +123,6 @@ struct TriLevels {                    // one level-scheduled strict triangle of 
     double2* dinv = nullptr;          // upper triangle: 1 / u_ii per slot (0 for padding)
     float2* dinv32 = nullptr;
     int64_t nnz = 0;
-    int grid64 = 0, grid32 = 0;       // co-resident blocks of the FP64 / FP32 solve kernels (0: not yet known)
 };
 
 struct ss_prec_s {
@@ -124,6 +132,7 @@ struct ss_prec_s {
     bool fp32 = false;                // FP32 copies of the triangles exist
     TriLevels lower, upper;
     int* err = nullptr;               // device error word (bounded waits)
+    unsigned long long* tickets = nullptr;  // block tickets of the lower [0] and upper [1] solves
     double2* tmp = nullptr;           // intermediate vector of the two solves (PENDING between uses)
     float2* tmp32 = nullptr;
     int64_t skipped_slot = -1;        // diagnostics: lower-solve slot whose row is not computed (-1: none)

@@ -42,3 +42,20 @@ int64_t ilut_host(int64_t n, const int32_t* row_ptr, const int32_t* col, const d
 // |a_ij|^2 (ties: ascending row).  val: interleaved complex.  Returns the
 // number of matched columns (n when the diagonal can be made zero-free).
 int64_t mbm_host(int64_t n, const int32_t* row_ptr, const int32_t* col, const double* val, int32_t* match);
+
+// Autotuner search of the batched solver's launch choices.  A choice is four
+// small integers: the lanes-per-row shifts of the lower triangle, the upper
+// triangle and A (G = rule G * 2^shift, shift in [TUNE_SHIFT_MIN,
+// TUNE_SHIFT_MAX]) and the level-staging flag (0: the rule's staging, 1: the
+// other one: the shared-memory ring for FP32, register prefetch for FP64).
+// Coordinate descent from `start`: each coordinate in turn tries its two
+// neighbours (cost evaluated once per choice, memoised) and moves while the
+// cost drops by more than 1 %; it stops when a full sweep improves nothing or
+// after max_probes evaluations.  Returns the number of evaluations.
+constexpr int TUNE_SHIFT_MIN = -1;
+constexpr int TUNE_SHIFT_MAX = 2;
+struct TuneChoice {
+    int lo, up, a, stage;
+};
+int tune_search(TuneChoice start, double (*cost)(const TuneChoice&, void*), void* user, int max_probes,
+                TuneChoice* best, double* best_cost);

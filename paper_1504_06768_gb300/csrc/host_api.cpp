@@ -72,3 +72,24 @@ extern "C" ss_status ss_mbm_host(int64_t n, const int32_t* row_ptr, const int32_
     *matched_out = mbm_host(n, row_ptr, col, val, match_out);
     return SS_OK;
 }
+
+namespace {
+double table_cost(const TuneChoice& c, void* user) {
+    const double* t = static_cast<const double*>(user);
+    const int span = TUNE_SHIFT_MAX - TUNE_SHIFT_MIN + 1;
+    return t[(((c.lo - TUNE_SHIFT_MIN) * span + (c.up - TUNE_SHIFT_MIN)) * span + (c.a - TUNE_SHIFT_MIN)) * 2 + c.stage];
+}
+}  // namespace
+
+extern "C" ss_status ss_tune_search_host(const double* cost_table, int32_t max_probes, int32_t* best_out,
+                                         int32_t* probes_out) {
+    if (!cost_table || !best_out || max_probes < 1) return SS_ERR_INVALID;
+    TuneChoice best{}, start{0, 0, 0, 0};
+    const int probes = tune_search(start, table_cost, const_cast<double*>(cost_table), max_probes, &best, nullptr);
+    best_out[0] = best.lo;
+    best_out[1] = best.up;
+    best_out[2] = best.a;
+    best_out[3] = best.stage;
+    if (probes_out) *probes_out = probes;
+    return SS_OK;
+}

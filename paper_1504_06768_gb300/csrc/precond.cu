@@ -71,26 +71,25 @@ template <> __device__ __forceinline__ float2 pending<float2>() {
     return make_float2(__uint_as_float(PENDING32), __uint_as_float(PENDING32));
 }
 
-// Sync-free triangular solve on a persistent grid.  Each triangle is stored
-// on its own in level order, cut into level-aligned units of R = 32 / G rows
-// (G lanes per row); a unit's entries are contiguous, so a warp reads them
-// as one coalesced run.  Units are dealt to the warps of a co-resident grid
-// round-robin (unit u to warp u mod W, each warp in increasing u), so every
-// dependency of a unit lies in a smaller unit, held by a running warp that
-// waits only on smaller units in turn: the solve always progresses, with no
-// atomics and no ticket.  The output vector starts filled with the PENDING
-// mark; a row waits (bounded) until the values it depends on are no longer
-// PENDING -- the value itself is the completion signal, so no flag or fence
-// is needed.  While a warp waits on its unit, the row records and the first
-// K entries per lane of its next unit, and the row records of the one after,
-// are already on their way: in the steady state a unit costs one dependent
-// round trip (the x values) once its inputs are ready.
+// Sync-free triangular solve.  Each triangle is stored on its own in level
+// order, cut into level-aligned units of R = 32 / G rows (G lanes per row); a
+// unit's entries are contiguous, so a warp reads them as one coalesced run.
+// Blocks take consecutive runs of units in level order through a ticket
+// counter (one atomic per block), so a row only ever waits for rows held by
+// earlier blocks, which are resident or finished: the solve always
+// progresses, whatever else runs on the device (no co-residency is needed).
+// The output vector starts filled with the PENDING mark; a row waits
+// (bounded) until the values it depends on are no longer PENDING -- the value
+// itself is the completion signal, so no flag or fence is needed.  A lane
+// issues the loads of its first K entries (columns, values, then the x they
+// need) together, so a row costs three dependent round trips (row record,
+// entries, x) once its inputs are ready.
 //   LOWER: x_i = b_i - sum_{j<i} l_ij x_j (unit diagonal); also re-marks
 //          `other[i]` (the upper solve's output) PENDING.
 //   UPPER: x_i = (b_i - sum_{j>i} u_ij x_j) / u_ii; afterwards re-marks b_i
 //          (the lower solve's output) PENDING for the next application.
 constexpr int TRSV_THREADS = 256;
-constexpr int TRSV_K = 2;      // entries per lane whose loads are issued together
+constexpr int TRSV_K = 4;      // entries per lane whose loads are issued together
 
 template <class T>
 struct TrsvArgs {
@@ -104,6 +103,7 @@ struct TrsvArgs {
     T* x;
     T* other;                  // lower: the upper solve's output (re-marked); upper: the lower's (b)
     int* err;
+    unsigned long long* ticket;   // block tickets of this triangle (never reset)
     const int* halt;
     unsigned long long wait_ns;
 };
@@ -172,61 +172,54 @@ __device__ __forceinline__ T wait_ready(const TrsvArgs<T>& a, int32_t c, T v, bo
 template <bool LOWER, int G, int K, class T>
 __global__ void __launch_bounds__(TRSV_THREADS) sptrsv_syncfree(TrsvArgs<T> a) {
     using C = Cplx<T>;
-    if (a.halt && *a.halt) return;      // uniform over the launch
+    if (a.halt && *a.halt) return;      // uniform over the launch: no ticket is taken
+    __shared__ unsigned long long s_ticket;
+    if (threadIdx.x == 0) s_ticket = atomicAdd(a.ticket, 1ull);
+    __syncthreads();
+    // the k-th block to start takes the k-th run of units (tickets keep counting
+    // across launches, each launch takes gridDim.x of them)
+    const int64_t u = (int64_t)(s_ticket % (unsigned long long)gridDim.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (u >= a.n_units) return;
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane % G;
-    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-    int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (u >= a.n_units) return;
     bool timed_out = false;
-    UnitPf<G, K, T> cur, nxt;
+    UnitPf<G, K, T> cur;
     unit_rows<LOWER, G, K, T>(a, u, grp, cur.i, cur.s, cur.e);
-    unit_rows<LOWER, G, K, T>(a, u + W, grp, nxt.i, nxt.s, nxt.e);
     unit_entries<LOWER, G, K, T>(a, u, grp, sub, cur);
-    for (; u < a.n_units; u += W) {
-        // requests for the next two units go out before this unit's wait
-        int32_t i2, s2, e2;
-        unit_rows<LOWER, G, K, T>(a, u + 2 * W, grp, i2, s2, e2);
-        unit_entries<LOWER, G, K, T>(a, u + W, grp, sub, nxt);
-        T xj[K];
+    T xj[K];
 #pragma unroll
-        for (int q = 0; q < K; ++q) xj[q] = cur.c[q] >= 0 ? __ldcv(&a.x[cur.c[q]]) : C::zero();
-        T acc = C::zero();
+    for (int q = 0; q < K; ++q) xj[q] = cur.c[q] >= 0 ? __ldcv(&a.x[cur.c[q]]) : C::zero();
+    T acc = C::zero();
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        if (cur.c[q] >= 0) acc = C::fma_(cur.v[q], wait_ready(a, cur.c[q], xj[q], timed_out), acc);
+    // entries beyond the first K G of a long row
+    for (int32_t base = cur.s + sub + K * G; base < cur.e; base += K * G) {
+        int32_t c[K];
+        T v[K], xv[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const int32_t k = base + q * G;
+            c[q] = k < cur.e ? __ldcs(&a.col[k]) : -1;
+            v[q] = k < cur.e ? __ldcs(&a.val[k]) : C::zero();
+        }
+#pragma unroll
+        for (int q = 0; q < K; ++q) xv[q] = c[q] >= 0 ? __ldcv(&a.x[c[q]]) : C::zero();
 #pragma unroll
         for (int q = 0; q < K; ++q)
-            if (cur.c[q] >= 0) acc = C::fma_(cur.v[q], wait_ready(a, cur.c[q], xj[q], timed_out), acc);
-        // entries beyond the first K G of a long row
-        for (int32_t base = cur.s + sub + K * G; base < cur.e; base += K * G) {
-            int32_t c[K];
-            T v[K], xv[K];
+            if (c[q] >= 0) acc = C::fma_(v[q], wait_ready(a, c[q], xv[q], timed_out), acc);
+    }
 #pragma unroll
-            for (int q = 0; q < K; ++q) {
-                const int32_t k = base + q * G;
-                c[q] = k < cur.e ? __ldcs(&a.col[k]) : -1;
-                v[q] = k < cur.e ? __ldcs(&a.val[k]) : C::zero();
-            }
-#pragma unroll
-            for (int q = 0; q < K; ++q) xv[q] = c[q] >= 0 ? __ldcv(&a.x[c[q]]) : C::zero();
-#pragma unroll
-            for (int q = 0; q < K; ++q)
-                if (c[q] >= 0) acc = C::fma_(v[q], wait_ready(a, c[q], xv[q], timed_out), acc);
-        }
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            T ov = C::shfl_down(acc, o);
-            acc.x += ov.x;
-            acc.y += ov.y;
-        }
-        if (cur.i >= 0 && sub == 0) {
-            T xi = C::sub(cur.bv, acc);
-            if (!LOWER) xi = C::mul(xi, cur.dv);
-            __stcg(&a.x[cur.i], xi);
-            if (a.other) __stcg(&a.other[cur.i], pending<T>());
-        }
-        cur = nxt;
-        nxt.i = i2;
-        nxt.s = s2;
-        nxt.e = e2;
+    for (int o = G / 2; o > 0; o >>= 1) {
+        T ov = C::shfl_down(acc, o);
+        acc.x += ov.x;
+        acc.y += ov.y;
+    }
+    if (cur.i >= 0 && sub == 0) {
+        T xi = C::sub(cur.bv, acc);
+        if (!LOWER) xi = C::mul(xi, cur.dv);
+        __stcg(&a.x[cur.i], xi);
+        if (a.other) __stcg(&a.other[cur.i], pending<T>());
     }
     if (__any_sync(FULL, timed_out) && lane == 0) atomicExch(a.err, 1);
 }
@@ -306,10 +299,11 @@ __global__ void check_missing_diag(const int32_t* __restrict__ dpos, int64_t n, 
 }
 
 // Lanes per row of a triangle: enough that K entries per lane cover a row of
-// the triangle's mean length, at least 2 (G divides 32).
+// twice the triangle's mean length in one batch of loads, at least 2 (G
+// divides 32).
 int trsv_lanes(double avg_row) {
     int g = 2;
-    while (g < 32 && g * TRSV_K < avg_row) g <<= 1;
+    while (g < 32 && g * TRSV_K < 2.0 * avg_row) g <<= 1;
     return g;
 }
 
@@ -430,9 +424,11 @@ static ss_status analyse(ss_ctx ctx, ss_prec M, const std::vector<int32_t>& hrp,
     SS_TRY(build_triangle(ctx, lower_order, lower_ptr, nl, true, hrp, hcol, M->lower));
     SS_TRY(build_triangle(ctx, upper_order, upper_ptr, nu, false, hrp, hcol, M->upper));
     SS_TRY(dev_alloc_n(ctx, &M->err, 1));
+    SS_TRY(dev_alloc_n(ctx, &M->tickets, 2));
     SS_TRY(dev_alloc_n(ctx, &M->tmp, (size_t)n));
     fill_pending<double2><<<(ss_count_launch(), 256), 256, 0, ctx->stream>>>(n, M->tmp);
     SS_CUDA(ctx, cudaMemsetAsync(M->err, 0, sizeof(int), ctx->stream));
+    SS_CUDA(ctx, cudaMemsetAsync(M->tickets, 0, 2 * sizeof(unsigned long long), ctx->stream));
     return SS_OK;
 }
 
@@ -507,24 +503,12 @@ ss_status prec_finish(ss_ctx ctx, ss_prec M, bool want_fp32) {
     return SS_OK;
 }
 
-// Launches one triangular solve on a co-resident grid (a cooperative launch,
-// so that every warp whose unit another waits on is running).
 template <bool LOWER, int G, class T>
-static ss_status launch_trsv_g(ss_ctx ctx, const TriLevels& L, int& grid_cache, TrsvArgs<T> a) {
-    auto kern = sptrsv_syncfree<LOWER, G, TRSV_K, T>;
+static ss_status launch_trsv_g(ss_ctx ctx, const TriLevels& L, TrsvArgs<T> a) {
     constexpr int wpb = TRSV_THREADS / 32;
-    if (grid_cache == 0) {
-        int per_sm = 0;
-        SS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TRSV_THREADS, 0));
-        if (per_sm < 1) return set_error(ctx, SS_ERR_CUDA, "triangular solve kernel cannot be resident");
-        grid_cache = per_sm * std::max(ctx->num_sms, 1);
-    }
-    const int64_t need = (L.n_units + wpb - 1) / wpb;
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, grid_cache));
-    void* args[] = {&a};
-    ss_count_launch();
-    SS_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(TRSV_THREADS), args, 0,
-                                             ctx->stream));
+    const int64_t blocks = (L.n_units + wpb - 1) / wpb;
+    sptrsv_syncfree<LOWER, G, TRSV_K, T><<<(ss_count_launch(), (unsigned)std::max<int64_t>(1, blocks)), TRSV_THREADS, 0,
+                                          ctx->stream>>>(a);
     return SS_OK;
 }
 
@@ -542,15 +526,15 @@ static ss_status launch_trsv(ss_ctx ctx, ss_prec M, TriLevels& L, const T* vals,
     a.x = x;
     a.other = other;
     a.err = M->err;
+    a.ticket = M->tickets + (LOWER ? 0 : 1);
     a.halt = halt;
     a.wait_ns = ctx->wait_ns;
-    int& gc = sizeof(T) == 16 ? L.grid64 : L.grid32;
     switch (L.g) {
-        case 2: return launch_trsv_g<LOWER, 2, T>(ctx, L, gc, a);
-        case 4: return launch_trsv_g<LOWER, 4, T>(ctx, L, gc, a);
-        case 8: return launch_trsv_g<LOWER, 8, T>(ctx, L, gc, a);
-        case 16: return launch_trsv_g<LOWER, 16, T>(ctx, L, gc, a);
-        default: return launch_trsv_g<LOWER, 32, T>(ctx, L, gc, a);
+        case 2: return launch_trsv_g<LOWER, 2, T>(ctx, L, a);
+        case 4: return launch_trsv_g<LOWER, 4, T>(ctx, L, a);
+        case 8: return launch_trsv_g<LOWER, 8, T>(ctx, L, a);
+        case 16: return launch_trsv_g<LOWER, 16, T>(ctx, L, a);
+        default: return launch_trsv_g<LOWER, 32, T>(ctx, L, a);
     }
 }
 
@@ -608,6 +592,7 @@ void prec_destroy(ss_ctx ctx, ss_prec M) {
     free_triangle(ctx, M->lower);
     free_triangle(ctx, M->upper);
     dev_free(ctx, M->err);
+    dev_free(ctx, M->tickets);
     dev_free(ctx, M->tmp);
     dev_free(ctx, M->tmp32);
 }

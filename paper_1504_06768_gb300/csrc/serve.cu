@@ -83,14 +83,15 @@ struct ss_server_s {
     PatternCache cache;
     SolutionCache sols;                  // warm starts (so.warm_start)
     std::vector<Slot> slots;
-    std::unique_ptr<ss_ctx_s> large_ctx;
+    std::vector<std::unique_ptr<ss_ctx_s>> large_ctx;   // one context (stream) per single-system worker
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<std::shared_ptr<Request>> q_fast, q_large;
     std::unordered_map<uint64_t, std::shared_ptr<Request>> live;
     uint64_t next_id = 1;
     bool stop = false;
-    std::thread worker, large_worker;
+    std::thread worker;
+    std::vector<std::thread> large_workers;
     std::string last_error;
     uint64_t waves = 0, completed = 0;
 };
@@ -206,7 +207,11 @@ void fast_lane(ss_server s) {
     }
 }
 
-void large_lane(ss_server s) {
+// Single-system requests: LARGE_WORKERS threads, each with its own stream, so
+// that several large solves (latency-bound chains of small launches) overlap.
+constexpr int LARGE_WORKERS = 2;
+
+void large_lane(ss_server s, int wid) {
     cudaSetDevice(s->device);
     while (true) {
         std::shared_ptr<Request> r;
@@ -222,22 +227,30 @@ void large_lane(ss_server s) {
             s->in_use += r->footprint;
         }
         ss_info inf{};
-        const ss_status st = steady_state(s->large_ctx.get(), &r->H.view, (int)r->cviews.size(),
+        const ss_status st = steady_state(s->large_ctx[wid].get(), &r->H.view, (int)r->cviews.size(),
                                           r->cviews.empty() ? nullptr : r->cviews.data(), &s->opt, r->rho_out, 0, &inf);
         if (st != SS_OK && st != SS_NOT_CONVERGED && st != SS_BREAKDOWN) {
             std::lock_guard<std::mutex> lock(s->mu);
-            s->last_error = s->large_ctx->last_error;
+            s->last_error = s->large_ctx[wid]->last_error;
         }
         finish(s, r, st, &inf);
     }
 }
 
-std::unique_ptr<ss_ctx_s> make_ctx(int device, int num_sms) {
+// high: the waves' streams (their blocks are scheduled first when SMs free
+// up); otherwise the lowest priority (the single-system lane, whose many small
+// launches would otherwise hold SMs a wave's whole-SM blocks are waiting for)
+std::unique_ptr<ss_ctx_s> make_ctx(int device, int num_sms, bool high) {
     std::unique_ptr<ss_ctx_s> c(new (std::nothrow) ss_ctx_s());
     if (!c) return nullptr;
     c->device = device;
     c->num_sms = num_sms;
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        least = greatest = 0;
+    }
+    if (cudaStreamCreateWithPriority(&c->stream, cudaStreamNonBlocking, high ? greatest : least) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
@@ -281,14 +294,16 @@ extern "C" ss_status ss_server_create(int device, const ss_options* opt, const s
     s->budget = s->so.hbm_budget_mb > 0 ? (size_t)(s->so.hbm_budget_mb * 1048576.0) : (size_t)(0.8 * (double)free_b);
     s->slots.resize(s->so.max_waves);
     for (Slot& sl : s->slots) {
-        sl.ctx = make_ctx(device, sms);
+        sl.ctx = make_ctx(device, sms, true);
         if (!sl.ctx) return SS_ERR_CUDA;
     }
-    s->large_ctx = make_ctx(device, sms);
-    if (!s->large_ctx) return SS_ERR_CUDA;
+    for (int k = 0; k < LARGE_WORKERS; ++k) {
+        s->large_ctx.push_back(make_ctx(device, sms, false));
+        if (!s->large_ctx.back()) return SS_ERR_CUDA;
+    }
     ss_server raw = s.get();
     s->worker = std::thread(fast_lane, raw);
-    s->large_worker = std::thread(large_lane, raw);
+    for (int k = 0; k < LARGE_WORKERS; ++k) s->large_workers.emplace_back(large_lane, raw, k);
     *out = s.release();
     return SS_OK;
 }
@@ -301,7 +316,8 @@ extern "C" ss_status ss_server_destroy(ss_server s) {
     }
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
-    if (s->large_worker.joinable()) s->large_worker.join();
+    for (auto& t : s->large_workers)
+        if (t.joinable()) t.join();
     cudaSetDevice(s->device);
     if (!s->slots.empty() && s->slots[0].ctx) {
         s->sols.clear(s->slots[0].ctx.get());       // stream-ordered frees on a slot stream, synchronised below
@@ -313,10 +329,11 @@ extern "C" ss_status ss_server_destroy(ss_server s) {
         }
         if (sl.pinned) cudaFreeHost(sl.pinned);
     }
-    if (s->large_ctx && s->large_ctx->stream) {
-        cudaStreamSynchronize(s->large_ctx->stream);
-        cudaStreamDestroy(s->large_ctx->stream);
-    }
+    for (auto& c : s->large_ctx)
+        if (c && c->stream) {
+            cudaStreamSynchronize(c->stream);
+            cudaStreamDestroy(c->stream);
+        }
     delete s;
     return SS_OK;
 }

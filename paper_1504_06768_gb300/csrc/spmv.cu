@@ -47,7 +47,7 @@ template <int G>
 static void launch_split(const DeviceCSR& A, const double2* x, double2* y, const int* halt, cudaStream_t s) {
     const int threads = 256;
     spmv_split_kernel<G, SPMV_K><<<(ss_count_launch(), grid_for(A.n_rows * G, threads)), threads, 0, s>>>(
-        A.s_row_ptr, A.s_col, A.s_val, A.n_rows, x, y, halt);
+        A.s_row_ptr, A.s_mid, A.s_col, A.s_val, A.n_rows, x, y, halt);
 }
 
 void spmv_launch(const DeviceCSR& A, const double2* x, double2* y, const int* halt, cudaStream_t s) {
@@ -110,15 +110,15 @@ __global__ void split_count(const int32_t* __restrict__ rp, const double2* __res
 
 __global__ void split_fill(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                            const double2* __restrict__ val, int64_t n, const int32_t* __restrict__ srp,
-                           uint32_t* __restrict__ scol, double* __restrict__ sval) {
+                           int32_t* __restrict__ smid, uint32_t* __restrict__ scol, double* __restrict__ sval) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t k = srp[i];
-    for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
-        const double2 a = val[t];
-        if (a.x != 0.0) { scol[k] = (uint32_t)col[t]; sval[k] = a.x; ++k; }
-        if (a.y != 0.0) { scol[k] = (uint32_t)col[t] | 0x80000000u; sval[k] = a.y; ++k; }
-    }
+    for (int32_t t = rp[i]; t < rp[i + 1]; ++t)          // real parts first
+        if (val[t].x != 0.0) { scol[k] = (uint32_t)col[t]; sval[k] = val[t].x; ++k; }
+    smid[i] = k;
+    for (int32_t t = rp[i]; t < rp[i + 1]; ++t)          // then the imaginary parts
+        if (val[t].y != 0.0) { scol[k] = (uint32_t)col[t]; sval[k] = val[t].y; ++k; }
 }
 
 }  // namespace
@@ -142,14 +142,18 @@ ss_status csr_split(ss_ctx ctx, DeviceCSR& A) {
     A.s_nnz = total;
     SS_TRY(dev_alloc_n(ctx, &A.s_col, (size_t)total));
     SS_TRY(dev_alloc_n(ctx, &A.s_val, (size_t)total));
+    SS_TRY(dev_alloc_n(ctx, &A.s_mid, (size_t)n));
     split_fill<<<(ss_count_launch(), grid_for(n, 256)), 256, 0, ctx->stream>>>(A.row_ptr, A.col, A.val, n,
-                                                                               A.s_row_ptr, A.s_col, A.s_val);
+                                                                               A.s_row_ptr, A.s_mid, A.s_col,
+                                                                               A.s_val);
     SS_CUDA(ctx, cudaGetLastError());
     A.s_state = 1;
     return SS_OK;
 }
 
 void csr_split_free(ss_ctx ctx, DeviceCSR& A) {
+    dev_free(ctx, A.s_mid);
+    A.s_mid = nullptr;
     dev_free(ctx, A.s_row_ptr);
     dev_free(ctx, A.s_col);
     dev_free(ctx, A.s_val);

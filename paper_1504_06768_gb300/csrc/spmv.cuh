@@ -66,13 +66,39 @@ __global__ void __launch_bounds__(256) spmv_kernel(const int32_t* __restrict__ r
     if (row < n && sub == 0) y[row] = acc;
 }
 
-// y = A x from the part-split copy of A (FP64): a part is one real value v
-// and a column word c (bit 31: the value is an imaginary part i v).  A real
-// part adds (v x.re, v x.im), an imaginary one (-v x.im, v x.re): two FMAs
-// against one x load, the operands picked by selects and the sign by a bit
-// flip, so the FP64 pipe only sees the FMAs and the lane reduction.
+// y = A x from the part-split copy of A (FP64): row i's real parts (value v,
+// column c: adds v x_c) come first, in [rp[i], mid[i]), then its imaginary
+// parts (value v of i v: adds i v x_c) in [mid[i], rp[i + 1]).  Two uniform
+// loops accumulate acc_r = sum v x_c over the real parts and acc_i over the
+// imaginary ones, y = acc_r + i acc_i: two FMAs per part against one x load,
+// and no operand selection, so the FP64 pipe only sees the FMAs and the lane
+// reduction.
 template <int G, int K>
-__global__ void __launch_bounds__(256) spmv_split_kernel(const int32_t* __restrict__ rp,
+__device__ __forceinline__ void split_segment(const uint32_t* __restrict__ col, const double* __restrict__ val,
+                                              const double2* __restrict__ x, int32_t a, int32_t b, int sub,
+                                              double2& acc) {
+    for (int32_t base = a + sub; base < b; base += K * G) {
+        uint32_t c[K];
+        double v[K];
+        double2 xv[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int32_t t = base + k * G;
+            c[k] = t < b ? __ldcs(&col[t]) : 0u;
+            v[k] = t < b ? __ldcs(&val[t]) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) xv[k] = __ldg(&x[c[k]]);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            acc.x = fma(v[k], xv[k].x, acc.x);
+            acc.y = fma(v[k], xv[k].y, acc.y);
+        }
+    }
+}
+
+template <int G, int K>
+__global__ void __launch_bounds__(256) spmv_split_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ mid,
                                                          const uint32_t* __restrict__ col,
                                                          const double* __restrict__ val, int64_t n,
                                                          const double2* __restrict__ x, double2* __restrict__ y,
@@ -81,32 +107,13 @@ __global__ void __launch_bounds__(256) spmv_split_kernel(const int32_t* __restri
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t row = gid / G;
     const int sub = threadIdx.x % G;
-    double2 acc = make_double2(0.0, 0.0);
+    double2 ar = make_double2(0.0, 0.0), ai = make_double2(0.0, 0.0);
     if (row < n) {
-        const int32_t a = rp[row], b = rp[row + 1];
-        for (int32_t base = a + sub; base < b; base += K * G) {
-            uint32_t c[K];
-            double v[K];
-            double2 xv[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const int32_t t = base + k * G;
-                c[k] = t < b ? __ldcs(&col[t]) : 0u;
-                v[k] = t < b ? __ldcs(&val[t]) : 0.0;
-            }
-#pragma unroll
-            for (int k = 0; k < K; ++k) xv[k] = __ldg(&x[c[k] & 0x7fffffffu]);
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const bool im = (c[k] >> 31) != 0u;
-                const double pr = im ? xv[k].y : xv[k].x;      // multiplies v into re(y)
-                const double pi = im ? xv[k].x : xv[k].y;      // and into im(y)
-                const double vr = __longlong_as_double(__double_as_longlong(v[k]) ^ ((long long)im << 63));
-                acc.x = fma(vr, pr, acc.x);
-                acc.y = fma(v[k], pi, acc.y);
-            }
-        }
+        const int32_t a = rp[row], m = mid[row], b = rp[row + 1];
+        split_segment<G, K>(col, val, x, a, m, sub, ar);
+        split_segment<G, K>(col, val, x, m, b, sub, ai);
     }
+    double2 acc = make_double2(ar.x - ai.y, ar.y + ai.x);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
         acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);

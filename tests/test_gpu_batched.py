@@ -145,3 +145,22 @@ def test_batched_device_and_host_views_agree(ss):
     assert st == 0, B.load().ss_last_error(ctx.handle).decode()
     for s, r, h in zip(systems, rho, host):
         assert np.array_equal(r.cpu().numpy().reshape((s.d, s.d), order="F"), h)
+
+
+def test_batched_autotune_same_states_and_cached_choice(ss):
+    """The autotuner times capped probe launches of candidate lanes-per-row
+    and staging choices and keeps the fastest; the states are the rule
+    choice's to the solve tolerance, the choice is reported per system and
+    kept for a second batch of the same shape."""
+    systems = [jaynes_cummings_rwa(seed=s, N=16) for s in range(24)]
+    pairs = [(s.H, s.c_ops) for s in systems]
+    for precision, td in (("mixed", 1e-8), ("fp64", 1e-10)):
+        ref, _ = ss.steady_state_batched(pairs, tol=1e-11, precision=precision)
+        tuned, ti = ss.steady_state_batched(pairs, tol=1e-11, precision=precision, autotune=True)
+        again, ai = ss.steady_state_batched(pairs, tol=1e-11, precision=precision, autotune=True)
+        for a, b, c, i in zip(ref, tuned, again, ti):
+            assert i["status"] == 0 and i["resid_Lrho"] <= 1e-11
+            assert trace_distance(a, b) <= td and np.array_equal(b, c)
+        assert all(-1 <= v <= 2 for v in ti[0]["tune_lanes_shift"]) and ti[0]["tune_stage"] in (0, 1)
+        assert ti[0]["tune_lanes_shift"] == ai[0]["tune_lanes_shift"] and ti[0]["tune_stage"] == ai[0]["tune_stage"]
+        assert trace_distance(tuned[3], steady_state_dense(systems[3].H, systems[3].c_ops)) <= td

@@ -92,3 +92,36 @@ def test_wait_limit_rejects_zero(ss):
     from paper_1504_06768_gb300 import _binding as B
     ctx = ss.get_context()
     assert B.load().ss_set_wait_limit(ctx.handle, 0) == 1
+
+
+def test_batched_staging_wait_runs_out_and_recovers(ss):
+    """The FP64 batched solver stages the levels of its triangular solves in
+    a shared-memory ring filled by bulk copies, each slot guarded by an
+    mbarrier whose wait is bounded.  ss_diag_batched_stall(5) makes every
+    block's sixth staging arm its barrier without issuing the copies (a
+    transfer that never arrives); with a 1 ms limit the waits give up, the
+    blocks stop staging, drain what they issued, and the call reports
+    SS_ERR_TIMEOUT.  The same context then solves correctly."""
+    from paper_1504_06768_gb300 import _binding as B
+    from oracle.metrics import trace_distance
+    from oracle.steady import steady_state_dense
+    lib = B.load()
+    systems = [jaynes_cummings_rwa(seed=s, N=12) for s in range(4)]
+    pairs = [(s.H, s.c_ops) for s in systems]
+    ctx = ss.get_context()
+    assert lib.ss_diag_batched_stall(ctx.handle, -2) == 1
+    assert lib.ss_set_wait_limit(ctx.handle, 1_000_000) == 0
+    assert lib.ss_diag_batched_stall(ctx.handle, 5) == 0
+    try:
+        t0 = time.perf_counter()
+        with pytest.raises(ss.SolverError) as e:
+            ss.steady_state_batched(pairs, tol=1e-10, precision="fp64", ctx=ctx)
+        assert e.value.status == SS_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 20.0
+    finally:
+        assert lib.ss_diag_batched_stall(ctx.handle, -1) == 0
+        assert lib.ss_set_wait_limit(ctx.handle, 2_000_000_000) == 0
+    rhos, infos = ss.steady_state_batched(pairs, tol=1e-10, precision="fp64", ctx=ctx)
+    for s, rho, info in zip(systems, rhos, infos):
+        assert info["status"] == 0
+        assert trace_distance(rho, steady_state_dense(s.H, s.c_ops)) <= 1e-9

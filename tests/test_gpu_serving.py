@@ -109,7 +109,7 @@ def test_served_sweep_warm_starts_from_earlier_requests(ss):
     earlier request with the same pattern: a drive sweep served point after
     point reaches the same states (against the cold server and the oracle)
     in fewer iterations, and a repeated request needs almost none."""
-    sweep = [jaynes_cummings_rwa(N=12, E=0.5 + 0.02 * k) for k in range(8)]
+    sweep = [jaynes_cummings_rwa(N=12, E=0.5 + 0.005 * k) for k in range(8)]
 
     def serve(warm):
         out = []

@@ -153,3 +153,44 @@ def test_mbm_host_on_trace_row_liouvillians(ss, name):
     ref, kr = weighted_mbm(A)
     assert k == kr == A.shape[0] and np.array_equal(match, ref)
     assert np.all(A[match, :].diagonal() != 0)
+
+
+# ------------------------------------------------------------- autotuner
+
+def _table(fn):
+    t = np.empty((4, 4, 4, 2))
+    for lo in range(4):
+        for up in range(4):
+            for a in range(4):
+                for st in range(2):
+                    t[lo, up, a, st] = fn(lo - 1, up - 1, a - 1, st)
+    return t
+
+
+def test_tune_search_finds_minimum_of_a_separable_bowl():
+    """Coordinate descent reaches the minimum of a separable cost (the rule
+    choice is (0, 0, 0, 0); the best is (1, -1, 2, 1))."""
+    import paper_1504_06768_gb300 as ss
+    t = _table(lambda lo, up, a, st: 10 + (lo - 1) ** 2 + 2 * (up + 1) ** 2 + 0.5 * (a - 2) ** 2 + (0 if st else 1))
+    best, probes = ss.tune_search_host(t)
+    assert best == (1, -1, 2, 1)
+    assert probes <= 4 * 4 * 4 * 2 and probes < 20           # memoised: far fewer than the whole table
+
+
+def test_tune_search_keeps_rule_choice_when_nothing_is_better_by_one_percent():
+    import paper_1504_06768_gb300 as ss
+    t = _table(lambda lo, up, a, st: 1.0 + 0.001 * (lo + up + a + st) ** 2)    # < 1 % apart everywhere
+    best, probes = ss.tune_search_host(t)
+    assert best == (0, 0, 0, 0)
+    assert probes == 1 + 2 + 2 + 2 + 1                        # the start and each coordinate's neighbours once
+
+
+def test_tune_search_stops_at_local_minimum_and_respects_probe_cap():
+    import paper_1504_06768_gb300 as ss
+    # an isolated global minimum that no single-coordinate move approaches
+    t = _table(lambda lo, up, a, st: 0.1 if (lo, up, a, st) == (2, 2, 2, 1) else
+               5 + abs(lo) + abs(up) + abs(a) + st)
+    best, probes = ss.tune_search_host(t)
+    assert best == (0, 0, 0, 0)
+    _, capped = ss.tune_search_host(_table(lambda lo, up, a, st: 10 - lo - up - a - st), max_probes=3)
+    assert capped == 3
