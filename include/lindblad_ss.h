@@ -381,7 +381,9 @@ ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_view* H, cons
  * one leaves idle.  Pattern analyses (RCM ordering, level schedule) stay
  * resident across waves for requests with the same structure.  Requests
  * outside the persistent solver's scope (n beyond its limit, or options it
- * does not run) go to a second lane running steady_state().  A request's
+ * does not run) go to a second lane running steady_state() in FP64 on two
+ * low-priority streams (its mixed form pays more iterations than it saves on
+ * systems that large), while the waves run on high-priority streams.  A request's
  * result is the one the same system gets alone from steady_state_batched
  * (or from steady_state in the second lane). */
 typedef struct ss_server_s* ss_server;

@@ -43,22 +43,28 @@ static void launch_f32(const DeviceCSR& A, const float2* val32, const float2* x,
         A.row_ptr, A.col, val32, A.n_rows, x, y, halt);
 }
 
+int spmv_split_group_size(int64_t n_rows, int64_t parts) {
+    const double avg = n_rows > 0 ? (double)parts / (double)n_rows : 1.0;
+    return avg <= 4.0 ? 2 : 4;
+}
+
+constexpr int SPLIT_K = 2;   // parts per lane whose loads are in flight together in the FP64 split SpMV
+
 template <int G>
 static void launch_split(const DeviceCSR& A, const double2* x, double2* y, const int* halt, cudaStream_t s) {
     const int threads = 256;
-    spmv_split_kernel<G, SPMV_K><<<(ss_count_launch(), grid_for(A.n_rows * G, threads)), threads, 0, s>>>(
+    spmv_split_kernel<G, SPLIT_K><<<(ss_count_launch(), grid_for(A.n_rows * G, threads)), threads, 0, s>>>(
         A.s_row_ptr, A.s_mid, A.s_col, A.s_val, A.n_rows, x, y, halt);
 }
 
 void spmv_launch(const DeviceCSR& A, const double2* x, double2* y, const int* halt, cudaStream_t s) {
     if (A.n_rows == 0) return;
     if (A.s_state == 1) {
-        switch (spmv_group_size(A.n_rows, A.s_nnz, false)) {
+        switch (spmv_split_group_size(A.n_rows, A.s_nnz)) {
+            case 1: launch_split<1>(A, x, y, halt, s); break;
             case 2: launch_split<2>(A, x, y, halt, s); break;
             case 4: launch_split<4>(A, x, y, halt, s); break;
-            case 8: launch_split<8>(A, x, y, halt, s); break;
-            case 16: launch_split<16>(A, x, y, halt, s); break;
-            default: launch_split<32>(A, x, y, halt, s); break;
+            default: launch_split<8>(A, x, y, halt, s); break;
         }
         return;
     }

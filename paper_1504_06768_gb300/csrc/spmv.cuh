@@ -68,12 +68,17 @@ __global__ void __launch_bounds__(256) spmv_kernel(const int32_t* __restrict__ r
 
 // y = A x from the part-split copy of A (FP64): row i's real parts (value v,
 // column c: adds v x_c) come first, in [rp[i], mid[i]), then its imaginary
-// parts (value v of i v: adds i v x_c) in [mid[i], rp[i + 1]).  Two uniform
-// loops accumulate acc_r = sum v x_c over the real parts and acc_i over the
-// imaginary ones, y = acc_r + i acc_i: two FMAs per part against one x load,
-// and no operand selection, so the FP64 pipe only sees the FMAs and the lane
-// reduction.
-template <int G, int K>
+// parts (value v of i v: adds i v x_c = (-v im x_c, v re x_c)) in
+// [mid[i], rp[i + 1]).  Two uniform loops accumulate into one complex sum,
+// the second with the operands swapped and one sign folded into the FMA: two
+// FMAs per part against one x load, no operand selection and no combining
+// step.  On GB300 a warp's FP64 instruction holds a sub-partition's FP64 pipe
+// for 64 cycles whatever its active lanes, so FP64 warp instructions (the
+// FMAs, the lanes that pad a step, the shuffle reduction) bound the kernel
+// along with its memory parallelism: four lanes per row and two parts per
+// lane in flight measured best on the chain (fewer lanes issue fewer FP64
+// instructions but keep fewer loads in flight).
+template <int G, int K, bool IMAG>
 __device__ __forceinline__ void split_segment(const uint32_t* __restrict__ col, const double* __restrict__ val,
                                               const double2* __restrict__ x, int32_t a, int32_t b, int sub,
                                               double2& acc) {
@@ -91,8 +96,13 @@ __device__ __forceinline__ void split_segment(const uint32_t* __restrict__ col, 
         for (int k = 0; k < K; ++k) xv[k] = __ldg(&x[c[k]]);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            acc.x = fma(v[k], xv[k].x, acc.x);
-            acc.y = fma(v[k], xv[k].y, acc.y);
+            if (IMAG) {
+                acc.x = fma(-v[k], xv[k].y, acc.x);
+                acc.y = fma(v[k], xv[k].x, acc.y);
+            } else {
+                acc.x = fma(v[k], xv[k].x, acc.x);
+                acc.y = fma(v[k], xv[k].y, acc.y);
+            }
         }
     }
 }
@@ -107,13 +117,12 @@ __global__ void __launch_bounds__(256) spmv_split_kernel(const int32_t* __restri
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t row = gid / G;
     const int sub = threadIdx.x % G;
-    double2 ar = make_double2(0.0, 0.0), ai = make_double2(0.0, 0.0);
+    double2 acc = make_double2(0.0, 0.0);
     if (row < n) {
         const int32_t a = rp[row], m = mid[row], b = rp[row + 1];
-        split_segment<G, K>(col, val, x, a, m, sub, ar);
-        split_segment<G, K>(col, val, x, m, b, sub, ai);
+        split_segment<G, K, false>(col, val, x, a, m, sub, acc);
+        split_segment<G, K, true>(col, val, x, m, b, sub, acc);
     }
-    double2 acc = make_double2(ar.x - ai.y, ar.y + ai.x);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
         acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
@@ -121,6 +130,10 @@ __global__ void __launch_bounds__(256) spmv_split_kernel(const int32_t* __restri
     }
     if (row < n && sub == 0) y[row] = acc;
 }
+
+// Lanes per row of the part-split FP64 SpMV: four, or two for rows of at
+// most four parts.
+int spmv_split_group_size(int64_t n_rows, int64_t parts);
 
 // Lanes per row for a mean row length (FP64: the FP64 pipe is the scarce unit,
 // fewer lanes per row; FP32: more lanes, more loads in flight).
