@@ -910,6 +910,22 @@ def cpu_baseline(sample: int):
                          "sample": f"2 JC40 systems by the oracle's dense FP64 LU (multithreaded BLAS), {dd:.1f} s"}}
 
 
+def run_kernels_only():
+    """The `spmv` block alone (chain and scaled optomechanics SpMV, chain
+    M^{-1} r), as one JSON object; used to profile those kernels."""
+    import contextlib
+    import torch
+    import __graft_entry__ as g
+    with contextlib.redirect_stdout(sys.stderr):
+        g.build()
+    import paper_1504_06768_gb300 as ss
+    from paper_1504_06768_gb300 import _binding as B
+    B.load()
+    stream = torch.cuda.current_stream()
+    ctx = ss.Context(0, stream)
+    return {"spmv": spmv_measure(ss, B, ctx, stream)}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -950,10 +966,15 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=300.0)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="only the chain / optomechanics SpMV and M^-1 r block (for profiling)")
     ap.add_argument("--cpu-sample", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if args.kernels_only:
+        out = run_kernels_only()
+    else:
+        out = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if out is not None:
         print(json.dumps(out))
 

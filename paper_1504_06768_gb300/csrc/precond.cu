@@ -224,6 +224,95 @@ __global__ void __launch_bounds__(TRSV_THREADS) sptrsv_syncfree(TrsvArgs<T> a) {
     if (__any_sync(FULL, timed_out) && lane == 0) atomicExch(a.err, 1);
 }
 
+// The same solve by one block for a system whose solution vector fits in
+// shared memory: x lives there, pre-marked PENDING, so a dependency is a
+// shared-memory store and load (tens of cycles) instead of a round trip
+// through L2 -- what counts for factors with many levels (ILUT's upper
+// triangle of the Jaynes-Cummings system: 5,703 levels for 6,400 rows).
+// Units are dealt to the block's warps round-robin (unit u to warp u mod W,
+// each warp in increasing u); every dependency lies in a smaller unit of a
+// warp of this block, so the solve progresses, and no barrier separates the
+// levels.  Each warp loads its next unit while it solves the current one.
+constexpr int TRSV_BLOCK_THREADS = 1024;
+
+template <class T>
+__device__ __forceinline__ T smem_ready_value(const TrsvArgs<T>& a, volatile T* xs, int32_t c, bool& timed_out) {
+    T v;
+    v.x = xs[c].x;
+    v.y = xs[c].y;
+    if (ready(v) || timed_out) return v;
+    const unsigned long long t0 = globaltimer_ns();
+    int spins = 0;
+    while (true) {
+        v.x = xs[c].x;
+        v.y = xs[c].y;
+        if (ready(v)) return v;
+        if ((++spins & 255) == 0 && (*(volatile int*)a.err != 0 || globaltimer_ns() - t0 > a.wait_ns)) {
+            if (*(volatile int*)a.err == 0) atomicExch(a.err, 1);
+            timed_out = true;
+            return Cplx<T>::zero();
+        }
+    }
+}
+
+template <bool LOWER, int G, int K, class T>
+__global__ void __launch_bounds__(TRSV_BLOCK_THREADS) sptrsv_block(TrsvArgs<T> a, int64_t n) {
+    using C = Cplx<T>;
+    if (a.halt && *a.halt) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    volatile T* xs = reinterpret_cast<volatile T*>(smem_raw);
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const T p = pending<T>();
+        xs[i].x = p.x;
+        xs[i].y = p.y;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G, sub = lane % G;
+    const int64_t W = blockDim.x >> 5;
+    bool timed_out = false;
+    UnitPf<G, K, T> cur, nxt;
+    int64_t u = threadIdx.x >> 5;
+    unit_rows<LOWER, G, K, T>(a, u, grp, cur.i, cur.s, cur.e);
+    unit_entries<LOWER, G, K, T>(a, u, grp, sub, cur);
+    for (; u < a.n_units; u += W) {
+        unit_rows<LOWER, G, K, T>(a, u + W, grp, nxt.i, nxt.s, nxt.e);
+        unit_entries<LOWER, G, K, T>(a, u + W, grp, sub, nxt);
+        T acc = C::zero();
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            if (cur.c[q] >= 0) acc = C::fma_(cur.v[q], smem_ready_value(a, xs, cur.c[q], timed_out), acc);
+        for (int32_t base = cur.s + sub + K * G; base < cur.e; base += K * G) {
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                const int32_t k = base + q * G;
+                if (k < cur.e) acc = C::fma_(a.val[k], smem_ready_value(a, xs, a.col[k], timed_out), acc);
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            T ov = C::shfl_down(acc, o);
+            acc.x += ov.x;
+            acc.y += ov.y;
+        }
+        if (cur.i >= 0 && sub == 0) {
+            T xi = C::sub(cur.bv, acc);
+            if (!LOWER) xi = C::mul(xi, cur.dv);
+            xs[cur.i].x = xi.x;
+            xs[cur.i].y = xi.y;
+        }
+        cur = nxt;
+    }
+    if (__any_sync(FULL, timed_out) && lane == 0) atomicExch(a.err, 1);
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        T v;
+        v.x = xs[i].x;
+        v.y = xs[i].y;
+        a.x[i] = v;
+    }
+}
+
 template <class T>
 __global__ void fill_pending(int64_t n, T* __restrict__ a) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -503,8 +592,21 @@ ss_status prec_finish(ss_ctx ctx, ss_prec M, bool want_fp32) {
     return SS_OK;
 }
 
+// Systems whose solution vector fits in a block's shared memory (at most this
+// many bytes) are solved by one block (sptrsv_block).
+constexpr size_t TRSV_BLOCK_MAX_BYTES = 200 * 1024;
+
 template <bool LOWER, int G, class T>
-static ss_status launch_trsv_g(ss_ctx ctx, const TriLevels& L, TrsvArgs<T> a) {
+static ss_status launch_trsv_g(ss_ctx ctx, const TriLevels& L, TrsvArgs<T> a, int64_t n) {
+    if ((size_t)n * sizeof(T) <= TRSV_BLOCK_MAX_BYTES) {
+        // FP64: one entry per lane per step (a padding lane still holds the FP64
+        // pipe for a whole warp instruction, and this path is a latency chain)
+        auto kern = sptrsv_block<LOWER, G, sizeof(T) == 16 ? 1 : TRSV_K, T>;
+        const size_t bytes = std::max<size_t>((size_t)n * sizeof(T), 16);
+        SS_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        kern<<<(ss_count_launch(), 1), TRSV_BLOCK_THREADS, bytes, ctx->stream>>>(a, n);
+        return SS_OK;
+    }
     constexpr int wpb = TRSV_THREADS / 32;
     const int64_t blocks = (L.n_units + wpb - 1) / wpb;
     sptrsv_syncfree<LOWER, G, TRSV_K, T><<<(ss_count_launch(), (unsigned)std::max<int64_t>(1, blocks)), TRSV_THREADS, 0,
@@ -530,11 +632,11 @@ static ss_status launch_trsv(ss_ctx ctx, ss_prec M, TriLevels& L, const T* vals,
     a.halt = halt;
     a.wait_ns = ctx->wait_ns;
     switch (L.g) {
-        case 2: return launch_trsv_g<LOWER, 2, T>(ctx, L, a);
-        case 4: return launch_trsv_g<LOWER, 4, T>(ctx, L, a);
-        case 8: return launch_trsv_g<LOWER, 8, T>(ctx, L, a);
-        case 16: return launch_trsv_g<LOWER, 16, T>(ctx, L, a);
-        default: return launch_trsv_g<LOWER, 32, T>(ctx, L, a);
+        case 2: return launch_trsv_g<LOWER, 2, T>(ctx, L, a, M->f.n_rows);
+        case 4: return launch_trsv_g<LOWER, 4, T>(ctx, L, a, M->f.n_rows);
+        case 8: return launch_trsv_g<LOWER, 8, T>(ctx, L, a, M->f.n_rows);
+        case 16: return launch_trsv_g<LOWER, 16, T>(ctx, L, a, M->f.n_rows);
+        default: return launch_trsv_g<LOWER, 32, T>(ctx, L, a, M->f.n_rows);
     }
 }
 
