@@ -446,6 +446,121 @@ __device__ void cta_trsv(const PackedOp& P, const int32_t* lvl, const int32_t* o
     }
 }
 
+// ------------------------------- sync-free triangular solves in one block
+// Mixed precision, without a barrier per level.  The output vector is first
+// filled with SF_PENDING, a NaN payload that no FP32 arithmetic yields (the
+// GPU's arithmetic returns its canonical NaN), and a row reads every value it
+// depends on until neither part holds that pattern: a value is its own
+// completion flag.  Unit u goes to warp u mod NW and each warp walks its
+// units in increasing order.  The units are level ordered, so every
+// dependency lies in an earlier unit and no row depends on a row of its own
+// unit: the earliest unfinished unit always has its inputs, and the block
+// cannot stall.  Waits are bounded all the same (the ring's limit; then the
+// abort flag and the error word are raised and the row goes on with zeros).
+constexpr uint32_t SF_PENDING = 0xFFBADBADu;
+
+__device__ __forceinline__ float2 sf_pending_value() {
+    return make_float2(__uint_as_float(SF_PENDING), __uint_as_float(SF_PENDING));
+}
+__device__ __forceinline__ float2 sf_load(const float2* p) {
+    float2 v;
+    asm volatile("ld.volatile.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(smem_u32(p)));
+    return v;
+}
+__device__ __forceinline__ void sf_store(float2* p, float2 v) {
+    asm volatile("st.volatile.shared.v2.f32 [%0], {%1, %2};\n" ::"r"(smem_u32(p)), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ bool sf_pending(float2 v) {
+    return __float_as_uint(v.x) == SF_PENDING || __float_as_uint(v.y) == SF_PENDING;
+}
+// The value at p once it is written, waiting at most rg.wait_ns.
+__device__ __forceinline__ float2 sf_wait(const float2* p, const Ring& rg) {
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t spin = 0;; ++spin) {
+        const float2 v = sf_load(p);
+        if (!sf_pending(v)) return v;
+        if ((spin & 63) == 63) {
+            if (*(volatile int*)rg.abort) break;
+            if (globaltimer_ns() - t0 > rg.wait_ns) {
+                *(volatile int*)rg.abort = 1;
+                atomicExch(rg.err, 1);
+                break;
+            }
+        }
+    }
+    return make_float2(0.f, 0.f);
+}
+__device__ __forceinline__ float2 sf_ready(const float2* p, const Ring& rg) {
+    const float2 v = sf_load(p);
+    return sf_pending(v) ? sf_wait(p, rg) : v;
+}
+
+// One unit's row update: x_i = rhs - sum_j t_ij x_j (times 1 / u_ii for the
+// upper triangle), all the row's x_j loads issued before any is tested.
+template <bool LOWER, int G>
+__device__ __forceinline__ void sf_row(const UnitRegs<float2>& cu, float2 rhs, const int32_t* __restrict__ ocol,
+                                       const float2* __restrict__ oval, float2* x, int sub, const Ring& rg) {
+    float2 xv[MAXE];
+#pragma unroll
+    for (int q = 0; q < MAXE; ++q) xv[q] = cu.jj[q] >= 0 ? sf_load(x + cu.jj[q]) : make_float2(0.f, 0.f);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < MAXE; ++q)
+        if (cu.jj[q] >= 0) {
+            if (sf_pending(xv[q])) xv[q] = sf_wait(x + cu.jj[q], rg);
+            acc = fmac(cu.vv[q], xv[q], acc);
+        }
+    for (int32_t k = cu.ob + sub; k < cu.oe; k += G) acc = fmac(oval[k], sf_ready(x + ocol[k], rg), acc);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        const float2 other = shd(acc, o);
+        acc.x += other.x;
+        acc.y += other.y;
+    }
+    if (cu.i >= 0 && sub == 0) {
+        float2 xi = subc(rhs, acc);
+        if (!LOWER) xi = mulc(xi, cu.dv);
+        sf_store(x + cu.i, xi);
+    }
+}
+
+// T x = rhs into x (filled with SF_PENDING and synchronised by the caller);
+// rhs is in shared memory.  Lower: rhs is complete when the solve starts.
+// Upper: rhs is the lower solve's output, waited on like a dependency.  Each
+// warp loads its next unit while it solves the current one; nothing on the
+// path of a unit waits for a global load.
+template <bool LOWER, int G>
+__device__ void cta_trsv_sfv(const PackedOp& P, const int32_t* __restrict__ ocol, const float2* __restrict__ oval,
+                             const float2* __restrict__ inv, const float2* rhs, float2* x, const Ring& rg) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane % G;
+    const bool dv = !LOWER && P.dinv != nullptr;   // packed 1 / u_ii, else from inv[]
+    UnitRegs<float2> ua, ub;
+    load_unit<G, float2>(P, warp, lane, ua, dv);
+    for (int32_t u = warp; u < P.nunits; u += NW) {
+        load_unit<G, float2>(P, u + NW, lane, ub, dv);
+        float2 b = make_float2(0.f, 0.f);
+        if (ua.i >= 0 && sub == 0) {
+            b = LOWER ? sf_load(rhs + ua.i) : sf_ready(rhs + ua.i, rg);
+            if (!LOWER && !dv) ua.dv = inv[ua.i];
+        }
+        sf_row<LOWER, G>(ua, b, ocol, oval, x, sub, rg);
+        ua = ub;
+    }
+}
+
+template <bool LOWER>
+__device__ void cta_trsv_sf(const PackedOp& P, const int32_t* ocol, const float2* oval, const float2* inv,
+                            const float2* rhs, float2* x, const Ring& rg) {
+    switch (P.G) {
+        case 1: cta_trsv_sfv<LOWER, 1>(P, ocol, oval, inv, rhs, x, rg); break;
+        case 2: cta_trsv_sfv<LOWER, 2>(P, ocol, oval, inv, rhs, x, rg); break;
+        case 4: cta_trsv_sfv<LOWER, 4>(P, ocol, oval, inv, rhs, x, rg); break;
+        case 8: cta_trsv_sfv<LOWER, 8>(P, ocol, oval, inv, rhs, x, rg); break;
+        case 16: cta_trsv_sfv<LOWER, 16>(P, ocol, oval, inv, rhs, x, rg); break;
+        default: cta_trsv_sfv<LOWER, 32>(P, ocol, oval, inv, rhs, x, rg); break;
+    }
+}
+
 // ------------------------------------------------------------------ SpMV
 // y = A x with x in shared memory, from the packed operand (consecutive
 // units); accumulates <rhat, y> (dots 0, 1) and |y|^2 (dot 2) when rhat is
@@ -539,6 +654,8 @@ struct Ctx {
     const T* fval;
     const T* finv;
     T* buf;                     // shared: n
+    T* buf2;                    // shared: n, the lower solve's output of the sync-free solves (null: level barriers)
+    T* buf3;                    // shared: n, the lower solve's right-hand side of the sync-free solves
     double* red;                // shared reduction scratch
     const int32_t* lvl_lo;      // level boundaries of the two triangles (shared, or global)
     const int32_t* lvl_up;
@@ -550,6 +667,8 @@ struct Ctx {
 struct SmemPlan {
     unsigned char* buf;
     unsigned char* pbuf;        // mixed precision: p^ (null: kept in global memory)
+    unsigned char* buf2;        // mixed precision, sync-free solves: the lower solve's output (else null)
+    unsigned char* buf3;        // and its right-hand side
     const int32_t* lvl_lo;
     const int32_t* lvl_up;
     Ring ring;
@@ -575,6 +694,19 @@ __device__ void cta_prec_staged(Ctx<T>& c, T* out) {
     const BatchSys& S = *c.S;
     cta_trsv<true, T>(S.lo, c.lvl_lo, S.f_col, c.fval, c.finv, c.buf, *c.ring);
     cta_trsv<false, T>(S.up, c.lvl_up, S.f_col, c.fval, c.finv, c.buf, *c.ring);
+    if (out)
+        for (int32_t i = threadIdx.x; i < c.n; i += BT) out[i] = c.buf[i];
+}
+
+// Mixed precision, sync-free: L y = b into buf2 (b in buf3), then U z = y
+// into buf, each without level barriers; z stays in buf and is also copied to
+// out when out is not null.  The caller's pass has written b to buf3, filled
+// buf and buf2 with SF_PENDING and synchronised.
+__device__ void cta_prec_sf(Ctx<float2>& c, float2* out) {
+    const BatchSys& S = *c.S;
+    cta_trsv_sf<true>(S.lo, S.f_col, c.fval, c.finv, c.buf3, c.buf2, *c.ring);
+    cta_trsv_sf<false>(S.up, S.f_col, c.fval, c.finv, c.buf2, c.buf, *c.ring);
+    __syncthreads();
     if (out)
         for (int32_t i = threadIdx.x; i < c.n; i += BT) out[i] = c.buf[i];
 }
@@ -874,6 +1006,8 @@ __device__ void solve_fp64(BatchSys& S, const BatchParams& P, SmemPlan& sm, doub
     c.fval = S.f_val;
     c.finv = S.f_inv;
     c.buf = reinterpret_cast<double2*>(sm.buf);
+    c.buf2 = nullptr;
+    c.buf3 = nullptr;
     c.red = red;
     c.lvl_lo = sm.lvl_lo;
     c.lvl_up = sm.lvl_up;
@@ -956,6 +1090,10 @@ __device__ void solve_mixed(BatchSys& S, const BatchParams& P, SmemPlan& sm, dou
     c.fval = S.f_val32;
     c.finv = S.f_inv32;
     c.buf = reinterpret_cast<float2*>(sm.buf);
+    c.buf2 = reinterpret_cast<float2*>(sm.buf2);
+    c.buf3 = reinterpret_cast<float2*>(sm.buf3);
+    const bool sf = c.buf2 != nullptr;
+    const float2 pend = sf_pending_value();
     c.red = red;
     c.lvl_lo = sm.lvl_lo;
     c.lvl_up = sm.lvl_up;
@@ -1018,14 +1156,21 @@ __device__ void solve_mixed(BatchSys& S, const BatchParams& P, SmemPlan& sm, dou
                         if (i < n) {
                             const T pi = (k == 1) ? ra[u] : addc(ra[u], mulc(bt, subc(pa[u], mulc(om, va[u]))));
                             p[i] = pi;
-                            c.buf[i] = pi;
+                            if (sf) {
+                                c.buf[i] = pend;
+                                c.buf2[i] = pend;
+                                c.buf3[i] = pi;
+                            } else {
+                                c.buf[i] = pi;
+                            }
                         }
                     }
                 }
             }
             __syncthreads();
-            cta_prec_staged<T>(c, ph);          // p^ = M^{-1} p, kept in ph
-            if (c.ring->umax > 0 && *(volatile int*)c.ring->abort) { status = SS_ERR_TIMEOUT; break; }
+            if (sf) cta_prec_sf(c, ph);         // p^ = M^{-1} p, kept in ph
+            else cta_prec_staged<T>(c, ph);
+            if ((sf || c.ring->umax > 0) && *(volatile int*)c.ring->abort) { status = SS_ERR_TIMEOUT; break; }
             A dv[3] = {0, 0, 0};
             cta_spmv<T>(S.pa, S.a_col, c.aval, c.buf, v, rhat, dv);
             double dvs[3];
@@ -1048,13 +1193,20 @@ __device__ void solve_mixed(BatchSys& S, const BatchParams& P, SmemPlan& sm, dou
                         if (i < n) {
                             const T si = subc(ra[u], mulc(al, va[u]));
                             s[i] = si;
-                            c.buf[i] = si;
+                            if (sf) {
+                                c.buf[i] = pend;
+                                c.buf2[i] = pend;
+                                c.buf3[i] = si;
+                            } else {
+                                c.buf[i] = si;
+                            }
                         }
                     }
                 }
             }
             __syncthreads();
-            cta_prec_staged<T>(c, nullptr);     // s^ = M^{-1} s stays in the solve buffer
+            if (sf) cta_prec_sf(c, nullptr);    // s^ = M^{-1} s stays in the solve buffer
+            else cta_prec_staged<T>(c, nullptr);
             A dz[3] = {0, 0, 0};
             cta_spmv<T>(S.pa, S.a_col, c.aval, c.buf, t, nullptr, dz);     // t = A s^
             __syncthreads();
@@ -1237,6 +1389,12 @@ __global__ void __launch_bounds__(BT, BATCH_BLOCKS_PER_SM) batched_solver(BatchS
                 sm.pbuf = smem + off;
                 off += vb;
             }
+            sm.buf2 = sm.buf3 = nullptr;
+            if (MIXED && P.sf) {
+                sm.buf2 = smem + off;
+                sm.buf3 = smem + off + vb;
+                off += 2 * vb;
+            }
             int32_t* lv = reinterpret_cast<int32_t*>(smem + off);
             if (P.lvl_smem) {
                 const int nlo = S.lo.nlev + 1, nup = S.up.nlev + 1;
@@ -1298,11 +1456,11 @@ size_t slot_bytes_of(int E, int R, int umax) {
 // (pbuf), the level boundaries (lvl_smem) and nslots ring slots of umax units.
 template <class T>
 size_t plan_bytes(const std::vector<BatchShape>& shapes, int pbuf, int lvl_smem, int umax, int nslots,
-                  size_t* slot_out) {
+                  size_t* slot_out, int sf = 0) {
     size_t base = 0, slot = 0;
     for (const BatchShape& b : shapes) {
         const size_t vb = ((size_t)b.n * sizeof(T) + 15) & ~size_t(15);
-        size_t v = vb * (pbuf ? 2 : 1);
+        size_t v = vb * (1 + (pbuf ? 1 : 0) + (sf ? 2 : 0));
         if (lvl_smem) v += ((size_t)(b.nlev_lo + b.nlev_up + 2) * 4 + 15) & ~size_t(15);
         base = std::max(base, v);
         if (umax > 0)
@@ -1329,6 +1487,21 @@ int widest_level(const std::vector<BatchShape>& shapes) {
 template <class T>
 size_t choose_plan(const std::vector<BatchShape>& shapes, size_t cap, BatchParams& p) {
     const bool ring_first = p.mixed ? p.stage_flip != 0 : p.stage_flip == 0;
+    p.sf = 0;
+    if (p.mixed && !ring_first)
+        for (int pbuf = 1; pbuf >= 0; --pbuf) {
+            size_t slot = 0;
+            const size_t b = plan_bytes<T>(shapes, pbuf, 0, 0, 0, &slot, 1);
+            if (b <= cap) {
+                p.sf = 1;
+                p.lvl_smem = 0;
+                p.pbuf_smem = pbuf;
+                p.ring_umax = 0;
+                p.ring_slots = 0;
+                p.ring_slot_bytes = 0;
+                return b;
+            }
+        }
     if (!ring_first)
         for (int pbuf = 1; pbuf >= 0; --pbuf)
             for (int lvl_smem = 1; lvl_smem >= 0; --lvl_smem) {

@@ -88,6 +88,7 @@ struct BatchParams {
     int ring_slot_bytes;
     int lvl_smem;               // level boundaries copied to shared memory
     int pbuf_smem;              // mixed precision: p^ kept in shared memory
+    int sf;                     // mixed precision: triangular solves without level barriers (values as flags)
 };
 
 struct BatchShape {             // what the shared-memory plan needs of one system
