@@ -107,10 +107,7 @@ struct ss_mat_s {
 struct TriLevels {                    // one level-scheduled strict triangle of the factors
     int32_t n_levels = 0;
     int32_t* order = nullptr;         // rows sorted by level (device, n)
-    int g = 32;                       // layout: R = 32 / g rows per unit
-    int g32 = 32, g64 = 32;           // lanes per row of the FP32 and FP64 solves (each >= g: a warp
-                                      // then takes 32 / g32 (32 / g64) rows of a unit, g32 / g (g64 / g)
-                                      // warps a unit)
+    int g = 32;                       // lanes per row in the solve (R = 32 / g rows per unit)
     int64_t n_units = 0;              // level-aligned units of R rows
     // The triangle in unit order, stored on its own: slot s = u R + k is the
     // k-th row of unit u (urow[s] = -1 pads a unit at the end of a level);
@@ -135,8 +132,7 @@ struct ss_prec_s {
     bool fp32 = false;                // FP32 copies of the triangles exist
     TriLevels lower, upper;
     int* err = nullptr;               // device error word (bounded waits)
-    unsigned long long* tickets = nullptr;  // block tickets of the lower [0] and upper [1] solves in FP64,
-                                            // [2] and [3] in FP32
+    unsigned long long* tickets = nullptr;  // block tickets of the lower [0] and upper [1] solves
     double2* tmp = nullptr;           // intermediate vector of the two solves (PENDING between uses)
     float2* tmp32 = nullptr;
     int64_t skipped_slot = -1;        // diagnostics: lower-solve slot whose row is not computed (-1: none)

@@ -78,10 +78,9 @@ template <> __device__ __forceinline__ float2 pending<float2>() {
 }
 
 // Sync-free triangular solve.  Each triangle is stored on its own in level
-// order, cut into level-aligned units of UR rows whose entries are contiguous,
-// so a warp reads them as one coalesced run.  A solve with G lanes per row
-// gives each warp 32 / G rows of a unit (G UR / 32 warps share a unit).
-// Blocks take consecutive runs of warp tasks in level order through a ticket
+// order, cut into level-aligned units of R = 32 / G rows (G lanes per row); a
+// unit's entries are contiguous, so a warp reads them as one coalesced run.
+// Blocks take consecutive runs of units in level order through a ticket
 // counter (one atomic per block), so a row only ever waits for rows held by
 // earlier blocks, which are resident or finished: the solve always
 // progresses, whatever else runs on the device (no co-residency is needed).
@@ -98,8 +97,7 @@ template <> __device__ __forceinline__ float2 pending<float2>() {
 //   UPPER: x_i = (b_i - sum_{j>i} u_ij x_j) / u_ii; afterwards re-marks b_i
 //          (the lower solve's output) PENDING for the next application.
 constexpr int TRSV_THREADS = 256;
-constexpr int TRSV_K = 4;      // FP32: entries per lane whose loads are issued together
-constexpr int TRSV_K64 = 4;    // the same for FP64
+constexpr int TRSV_K = 4;      // entries per lane whose loads are issued together
 // Systems whose solution vector fits in a block's shared memory (at most this
 // many bytes) are solved by one block (sptrsv_block).
 constexpr size_t TRSV_BLOCK_MAX_BYTES = 200 * 1024;
@@ -112,7 +110,6 @@ struct TrsvArgs {
     const T* val;
     const T* dinv;             // upper: 1 / u_ii per slot
     int64_t n_units;
-    int32_t ur;                // rows per unit
     const T* b;
     T* x;
     T* other;                  // lower: the upper solve's output (re-marked); upper: the lower's (b)
@@ -130,19 +127,16 @@ struct UnitPf {                // one lane's share of a unit, prefetched
     T bv, dv;                  // b_i and 1 / u_ii (lane sub == 0)
 };
 
-// Rows of warp task t (G lanes per row): unit t / S, its slice t mod S of
-// 32 / G rows, S = G UR / 32.  Slot of this lane's row, its row id (-1:
+// Slot of this lane's row in unit u (G lanes per row), its row id (-1:
 // padding or past the end) and entry range.
 template <int G, class T>
-__device__ __forceinline__ void task_rows(const TrsvArgs<T>& a, int64_t t, int grp, int64_t& slot, int32_t& i,
+__device__ __forceinline__ void unit_rows(const TrsvArgs<T>& a, int64_t u, int grp, int64_t& slot, int32_t& i,
                                           int32_t& s, int32_t& e) {
-    const int64_t S = (int64_t)a.ur * G / 32;
-    const int64_t u = t / S;
     i = -1;
     s = e = 0;
     slot = 0;
     if (u < a.n_units) {
-        slot = u * a.ur + (t - u * S) * (32 / G) + grp;
+        slot = u * (32 / G) + grp;
         i = __ldg(&a.urow[slot]);
         s = __ldg(&a.uptr[slot]);
         e = __ldg(&a.uptr[slot + 1]);
@@ -150,7 +144,7 @@ __device__ __forceinline__ void task_rows(const TrsvArgs<T>& a, int64_t t, int g
 }
 
 template <bool LOWER, int G, int K, class T>
-__device__ __forceinline__ void task_entries(const TrsvArgs<T>& a, int64_t slot, int sub, UnitPf<G, K, T>& p) {
+__device__ __forceinline__ void unit_entries(const TrsvArgs<T>& a, int64_t slot, int sub, UnitPf<G, K, T>& p) {
     using C = Cplx<T>;
 #pragma unroll
     for (int q = 0; q < K; ++q) {
@@ -193,17 +187,17 @@ __global__ void __launch_bounds__(TRSV_THREADS) sptrsv_syncfree(TrsvArgs<T> a) {
     __shared__ unsigned long long s_ticket;
     if (threadIdx.x == 0) s_ticket = atomicAdd(a.ticket, 1ull);
     __syncthreads();
-    // the k-th block to start takes the k-th run of warp tasks (tickets keep
+    // the k-th block to start takes the k-th run of units (tickets keep
     // counting across launches, each launch takes gridDim.x of them)
-    const int64_t t = (int64_t)(s_ticket % (unsigned long long)gridDim.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (t >= a.n_units * ((int64_t)a.ur * G / 32)) return;
+    const int64_t u = (int64_t)(s_ticket % (unsigned long long)gridDim.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (u >= a.n_units) return;
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane % G;
     bool timed_out = false;
     UnitPf<G, K, T> cur;
     int64_t slot;
-    task_rows<G, T>(a, t, grp, slot, cur.i, cur.s, cur.e);
-    task_entries<LOWER, G, K, T>(a, slot, sub, cur);
+    unit_rows<G, T>(a, u, grp, slot, cur.i, cur.s, cur.e);
+    unit_entries<LOWER, G, K, T>(a, slot, sub, cur);
     T xj[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) xj[q] = cur.c[q] >= 0 ? __ldcv(&a.x[cur.c[q]]) : C::zero();
@@ -266,11 +260,10 @@ __global__ void __launch_bounds__(TRSV_THREADS) sptrsv_syncfree(TrsvArgs<T> a) {
 // shared-memory store and load (tens of cycles) instead of a round trip
 // through L2 -- what counts for factors with many levels (ILUT's upper
 // triangle of the Jaynes-Cummings system: 5,703 levels for 6,400 rows).
-// Warp tasks are dealt to the block's warps round-robin (task t to warp t mod
-// W, each warp in increasing t); every dependency lies in an earlier unit,
-// hence in a smaller task of a warp of this block, so the solve progresses,
-// and no barrier separates the levels.  Each warp loads its next task while
-// it solves the current one.
+// Units are dealt to the block's warps round-robin (unit u to warp u mod W,
+// each warp in increasing u); every dependency lies in a smaller unit of a
+// warp of this block, so the solve progresses, and no barrier separates the
+// levels.  Each warp loads its next unit while it solves the current one.
 constexpr int TRSV_BLOCK_THREADS = 1024;
 
 template <class T>
@@ -310,13 +303,12 @@ __global__ void __launch_bounds__(TRSV_BLOCK_THREADS) sptrsv_block(TrsvArgs<T> a
     const int64_t W = blockDim.x >> 5;
     bool timed_out = false;
     UnitPf<G, K, T> cur, nxt;
-    const int64_t n_tasks = a.n_units * ((int64_t)a.ur * G / 32);
-    int64_t t = threadIdx.x >> 5, slot;
-    task_rows<G, T>(a, t, grp, slot, cur.i, cur.s, cur.e);
-    task_entries<LOWER, G, K, T>(a, slot, sub, cur);
-    for (; t < n_tasks; t += W) {
-        task_rows<G, T>(a, t + W, grp, slot, nxt.i, nxt.s, nxt.e);
-        task_entries<LOWER, G, K, T>(a, slot, sub, nxt);
+    int64_t u = threadIdx.x >> 5, slot;
+    unit_rows<G, T>(a, u, grp, slot, cur.i, cur.s, cur.e);
+    unit_entries<LOWER, G, K, T>(a, slot, sub, cur);
+    for (; u < a.n_units; u += W) {
+        unit_rows<G, T>(a, u + W, grp, slot, nxt.i, nxt.s, nxt.e);
+        unit_entries<LOWER, G, K, T>(a, slot, sub, nxt);
         T acc = C::zero();
 #pragma unroll
         for (int q = 0; q < K; ++q)
@@ -447,13 +439,7 @@ ss_status build_triangle(ss_ctx ctx, const std::vector<int32_t>& order, const st
     int64_t nnz_t = 0;
     for (int64_t i = 0; i < n; ++i)
         for (int32_t t = hrp[i]; t < hrp[i + 1]; ++t) nnz_t += lower ? hcol[t] < i : hcol[t] > i;
-    T.g32 = trsv_lanes(n ? (double)nnz_t / n : 1.0);
-    // FP64 with one lane per row and ten entries per lane, which issues the
-    // fewest FP64 instructions, measured slower on the chain (2,333 against
-    // 1,853 us per M^-1 r): a row's dependent FP64 instructions are the
-    // latency of a level
-    T.g64 = T.g32;
-    T.g = std::min(T.g32, T.g64);
+    T.g = trsv_lanes(n ? (double)nnz_t / n : 1.0);
     const int R = 32 / T.g;
     std::vector<int32_t> urow;
     level_units_host(order, lptr, R, urow);
@@ -558,11 +544,11 @@ static ss_status analyse(ss_ctx ctx, ss_prec M, const std::vector<int32_t>& hrp,
     SS_TRY(build_triangle(ctx, lower_order, lower_ptr, nl, true, hrp, hcol, M->lower));
     SS_TRY(build_triangle(ctx, upper_order, upper_ptr, nu, false, hrp, hcol, M->upper));
     SS_TRY(dev_alloc_n(ctx, &M->err, 1));
-    SS_TRY(dev_alloc_n(ctx, &M->tickets, 4));
+    SS_TRY(dev_alloc_n(ctx, &M->tickets, 2));
     SS_TRY(dev_alloc_n(ctx, &M->tmp, (size_t)n));
     fill_pending<double2><<<(ss_count_launch(), 256), 256, 0, ctx->stream>>>(n, M->tmp);
     SS_CUDA(ctx, cudaMemsetAsync(M->err, 0, sizeof(int), ctx->stream));
-    SS_CUDA(ctx, cudaMemsetAsync(M->tickets, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    SS_CUDA(ctx, cudaMemsetAsync(M->tickets, 0, 2 * sizeof(unsigned long long), ctx->stream));
     return SS_OK;
 }
 
@@ -649,10 +635,9 @@ static ss_status launch_trsv_g(ss_ctx ctx, const TriLevels& L, TrsvArgs<T> a, in
         return SS_OK;
     }
     constexpr int wpb = TRSV_THREADS / 32;
-    const int64_t tasks = L.n_units * ((int64_t)a.ur * G / 32);
-    const int64_t blocks = (tasks + wpb - 1) / wpb;
-    sptrsv_syncfree<LOWER, G, sizeof(T) == 16 ? TRSV_K64 : TRSV_K, T>
-        <<<(ss_count_launch(), (unsigned)std::max<int64_t>(1, blocks)), TRSV_THREADS, 0, ctx->stream>>>(a);
+    const int64_t blocks = (L.n_units + wpb - 1) / wpb;
+    sptrsv_syncfree<LOWER, G, TRSV_K, T><<<(ss_count_launch(), (unsigned)std::max<int64_t>(1, blocks)), TRSV_THREADS, 0,
+                                          ctx->stream>>>(a);
     return SS_OK;
 }
 
@@ -666,18 +651,14 @@ static ss_status launch_trsv(ss_ctx ctx, ss_prec M, TriLevels& L, const T* vals,
     a.val = vals;
     a.dinv = dinv;
     a.n_units = L.n_units;
-    a.ur = 32 / L.g;
     a.b = b;
     a.x = x;
     a.other = other;
     a.err = M->err;
-    // a launch takes gridDim.x tickets, and the grid depends on the precision's
-    // lanes per row: one counter per triangle and precision
-    a.ticket = M->tickets + (LOWER ? 0 : 1) + (sizeof(T) == 16 ? 0 : 2);
+    a.ticket = M->tickets + (LOWER ? 0 : 1);
     a.halt = halt;
     a.wait_ns = ctx->wait_ns;
-    switch (sizeof(T) == 16 ? L.g64 : L.g32) {
-        case 1: return launch_trsv_g<LOWER, 1, T>(ctx, L, a, M->f.n_rows);
+    switch (L.g) {
         case 2: return launch_trsv_g<LOWER, 2, T>(ctx, L, a, M->f.n_rows);
         case 4: return launch_trsv_g<LOWER, 4, T>(ctx, L, a, M->f.n_rows);
         case 8: return launch_trsv_g<LOWER, 8, T>(ctx, L, a, M->f.n_rows);
