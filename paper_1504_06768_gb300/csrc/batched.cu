@@ -528,7 +528,9 @@ __device__ __forceinline__ void sf_row(const UnitRegs<float2>& cu, float2 rhs, c
 // rhs is in shared memory.  Lower: rhs is complete when the solve starts.
 // Upper: rhs is the lower solve's output, waited on like a dependency.  Each
 // warp loads its next unit while it solves the current one; nothing on the
-// path of a unit waits for a global load.
+// path of a unit waits for a global load.  (Three units in registers, each
+// requested two unit solves ahead, put them in local memory: 1,514-1,525
+// against 1,964-1,967 solves/s on 608 JC40 systems.)
 template <bool LOWER, int G>
 __device__ void cta_trsv_sfv(const PackedOp& P, const int32_t* __restrict__ ocol, const float2* __restrict__ oval,
                              const float2* __restrict__ inv, const float2* rhs, float2* x, const Ring& rg) {
@@ -577,11 +579,13 @@ __device__ void cta_spmv_pk(const PackedOp& P, const int32_t* __restrict__ ocol,
     for (int32_t base = warp; base < P.nunits; base += NW * SPMV_UNROLL) {
         UnitRegs<T> ur[SPMV_UNROLL];
         T hr[SPMV_UNROLL];
+        // every unit's loads first, then the r^ values their row records
+        // point to: one round trip for the units instead of one per unit
 #pragma unroll
-        for (int k = 0; k < SPMV_UNROLL; ++k) {
-            load_unit<G, T>(P, base + k * NW, lane, ur[k]);
+        for (int k = 0; k < SPMV_UNROLL; ++k) load_unit<G, T>(P, base + k * NW, lane, ur[k]);
+#pragma unroll
+        for (int k = 0; k < SPMV_UNROLL; ++k)
             hr[k] = (rhat && ur[k].i >= 0 && sub == 0) ? rhat[ur[k].i] : zero<T>();
-        }
 #pragma unroll
         for (int k = 0; k < SPMV_UNROLL; ++k) {
             T acc = zero<T>();
@@ -1038,27 +1042,93 @@ __device__ void solve_fp64(BatchSys& S, const BatchParams& P, SmemPlan& sm, doub
     S.status = status;
 }
 
+// r64 = b - A x64 over the packed A (G lanes per row): the slots' columns
+// and CSR positions, then the FP64 values (gathered from the CSR) and the x
+// they select, TRU units per warp with their loads in flight together; the
+// entries of long rows beyond their slots come from the CSR.  Adds |r_i|^2
+// of this thread's rows to nrm.
+constexpr int TRU = 2;
+
+template <int G>
+__device__ void cta_residual_pk(const BatchSys& S, const double2* __restrict__ x64, double2* __restrict__ r64,
+                                float2* __restrict__ r32, double& nrm) {
+    const PackedOp& P = S.pa;
+    constexpr int R = 32 / G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane / G, sub = lane % G;
+    const int E = P.E;
+    const double2* __restrict__ av = S.a_val;
+    const int32_t* __restrict__ ac = S.a_col;
+    for (int32_t base = warp; base < P.nunits; base += NW * TRU) {
+        int4 m[TRU];
+        int32_t jj[TRU][MAXE], kk[TRU][MAXE];
+#pragma unroll
+        for (int t = 0; t < TRU; ++t) {
+            const int32_t u = base + t * NW;
+            m[t] = make_int4(-1, 0, 0, 0);
+#pragma unroll
+            for (int q = 0; q < MAXE; ++q) jj[t][q] = kk[t][q] = -1;
+            if (u < P.nunits) {
+                m[t] = P.meta[u * R + grp];
+#pragma unroll
+                for (int q = 0; q < MAXE; ++q)
+                    if (q < E) {
+                        const int64_t slot = ((int64_t)u * E + q) * 32 + lane;
+                        jj[t][q] = P.col[slot];
+                        kk[t][q] = P.src[slot];
+                    }
+            }
+        }
+        double2 a[TRU][MAXE], xv[TRU][MAXE];
+#pragma unroll
+        for (int t = 0; t < TRU; ++t)
+#pragma unroll
+            for (int q = 0; q < MAXE; ++q) {
+                a[t][q] = kk[t][q] >= 0 ? av[kk[t][q]] : zero<double2>();
+                xv[t][q] = jj[t][q] >= 0 ? x64[jj[t][q]] : zero<double2>();
+            }
+#pragma unroll
+        for (int t = 0; t < TRU; ++t) {
+            double2 acc = zero<double2>();
+#pragma unroll
+            for (int q = 0; q < MAXE; ++q)
+                if (jj[t][q] >= 0) acc = fmac(a[t][q], xv[t][q], acc);
+#pragma unroll 4
+            for (int32_t k = m[t].y + sub; k < m[t].z; k += G) acc = fmac(av[k], x64[ac[k]], acc);
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) {
+                const double2 other = shd(acc, o);
+                acc.x += other.x;
+                acc.y += other.y;
+            }
+            const int32_t i = m[t].x;
+            if (i >= 0 && sub == 0) {
+                const double2 y = make_double2((i == S.r0 ? S.w : 0.0) - acc.x, -acc.y);
+                r64[i] = y;
+                r32[i] = make_float2((float)y.x, (float)y.y);
+                nrm += y.x * y.x + y.y * y.y;
+            }
+        }
+    }
+}
+
 // True residual in FP64: r64 = b - A x64 (b = w e_r0), r32 = r64 rounded to
 // FP32; returns ||r64||_2 and, in *lr, ||L rho||_2 for rho = x64 / tr(x64)
 // (L x = b - r64 - w tr(x) e_r0, so no second product is needed).
 __device__ double true_residual(const BatchSys& S, const double2* __restrict__ x64, double2* __restrict__ r64,
                                 float2* __restrict__ r32, double* red, double* lr) {
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int32_t i = threadIdx.x; i < S.n; i += BT) {
-        double2 y = make_double2(i == S.r0 ? S.w : 0.0, 0.0);
-        for (int32_t k = S.a_rp[i]; k < S.a_rp[i + 1]; ++k) {
-            const double2 a = S.a_val[k], xv = x64[S.a_col[k]];
-            y.x -= a.x * xv.x - a.y * xv.y;
-            y.y -= a.x * xv.y + a.y * xv.x;
-        }
-        r64[i] = y;
-        r32[i] = make_float2((float)y.x, (float)y.y);
-        acc[0] += y.x * y.x + y.y * y.y;
-        if (i < S.d) {
-            const double2 v = x64[S.tidx[i]];
-            acc[1] += v.x;
-            acc[2] += v.y;
-        }
+    switch (S.pa.G) {
+        case 1: cta_residual_pk<1>(S, x64, r64, r32, acc[0]); break;
+        case 2: cta_residual_pk<2>(S, x64, r64, r32, acc[0]); break;
+        case 4: cta_residual_pk<4>(S, x64, r64, r32, acc[0]); break;
+        case 8: cta_residual_pk<8>(S, x64, r64, r32, acc[0]); break;
+        case 16: cta_residual_pk<16>(S, x64, r64, r32, acc[0]); break;
+        default: cta_residual_pk<32>(S, x64, r64, r32, acc[0]); break;
+    }
+    for (int32_t i = threadIdx.x; i < S.d; i += BT) {
+        const double2 v = x64[S.tidx[i]];
+        acc[1] += v.x;
+        acc[2] += v.y;
     }
     cta_sum<3>(acc, red);
     const double2 tr = make_double2(acc[1], acc[2]);
@@ -1477,13 +1547,15 @@ int widest_level(const std::vector<BatchShape>& shapes) {
     return std::min(u, NW);
 }
 
-// Mixed precision (FP32 operands): no ring.  Each warp loads its unit of the
-// next level into registers before the current level's barrier, which is
-// faster than the ring for these operands (JC40, 608 systems: 347.5 against
-// 360.1 ms); p^ and the level boundaries go to shared memory.  FP64: a deep
-// ring (every level's data is requested nslots - 1 levels ahead, which has
-// to cover the memory latency; 449.9 against 632.1 ms without it), level
-// boundaries in shared memory first.
+// Mixed precision (FP32 operands): the sync-free solves (three more shared
+// vectors, and p^ in shared memory when it fits; JC40, 608 systems: 313-317
+// against 338-344 ms per step with level barriers), else level barriers with
+// each warp loading its unit of the next level into registers before the
+// current level's barrier, which is faster than the ring for these operands
+// (347.5 against 360.1 ms); p^ and the level boundaries go to shared memory.
+// FP64: a deep ring (every level's data is requested nslots - 1 levels
+// ahead, which has to cover the memory latency; 449.9 against 632.1 ms
+// without it), level boundaries in shared memory first.
 template <class T>
 size_t choose_plan(const std::vector<BatchShape>& shapes, size_t cap, BatchParams& p) {
     const bool ring_first = p.mixed ? p.stage_flip != 0 : p.stage_flip == 0;
