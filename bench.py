@@ -687,6 +687,8 @@ def configs_measure(ss):
         c3[prec] = {"solves_per_s": len(opto) / dt, "s_per_solve": dt / len(opto),
                     "iters": [o[1]["iters"] for o in out], "resid_Lrho": [o[1]["resid_Lrho"] for o in out],
                     "converged": sum(o[1]["status"] == 0 for o in out)}
+        if prec == "mixed":
+            c3[prec]["fp64_fallback"] = [o[1]["fp64_fallback"] for o in out]
     c3["trace_distance_mixed_vs_fp64"] = _td_stats(_td_list(ro["mixed"], ro["fp64"]))
     res["optomechanics"] = c3
 

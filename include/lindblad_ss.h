@@ -137,6 +137,9 @@ typedef struct {
     int32_t tune_lanes_shift[3];         /* batched solver: lanes per row of the lower triangle, the
                                             upper triangle and L~ as log2 multiples of the rule's choice */
     int32_t tune_stage;                  /* 1: the level staging other than the rule's (see autotune)  */
+    int32_t fp64_fallback;               /* MIXED single-system solve: 1 = an FP32 inner solve stalled
+                                            (did not reach inner_rtol within its cap) and the remaining
+                                            iterations ran in FP64 from the refined iterate            */
 } ss_info;
 
 /* ---------------------------------------------------------------- context */

@@ -45,7 +45,7 @@ class Info(C.Structure):
                 ("nnz_factors", C.c_int64), ("levels_lower", C.c_int32), ("levels_upper", C.c_int32),
                 ("ms_setup", C.c_double), ("ms_solve", C.c_double), ("method", C.c_int),
                 ("bw_modified", C.c_int64), ("bw_shifted", C.c_int64),
-                ("tune_lanes_shift", C.c_int32 * 3), ("tune_stage", C.c_int32)]
+                ("tune_lanes_shift", C.c_int32 * 3), ("tune_stage", C.c_int32), ("fp64_fallback", C.c_int32)]
 
     def as_dict(self) -> dict:
         out = {k: getattr(self, k) for k, _ in self._fields_}

@@ -678,8 +678,31 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
 
     double lr = INFINITY;
     int status = SS_NOT_CONVERGED, total = 0, outer = 0;
+    bool fp64_fallback = false;
     const int64_t r0 = iperm[0];
     KrylovResultHost res;
+    // FP64 BiCGSTAB/GMRES from the current x on the trace-row system until
+    // ||L rho|| <= tol or the iteration budget is spent
+    auto fp64_passes = [&]() -> ss_status {
+        double inner = 0.5 * opt.tol;
+        for (int pass = 0; pass < 8; ++pass) {
+            int left = opt.maxiter - total;
+            if (krylov == SS_KRYLOV_GMRES)
+                SS_TRY(gmres_dev(ctx, Ap->m, M, kw, b, x, inner, left, opt.restart, &res, nullptr, kaug));
+            else
+                SS_TRY(bicgstab_dev(ctx, Ap->m, M, kw, b, x, inner, left, &res));
+            total += res.iters;
+            SS_TRY(su_lrho(ctx, Ap->m, x, 0, w_used, r0, d, tidx_d, y, scr, trace_d, &lr, nullptr));
+            if (lr <= opt.tol) { status = SS_OK; break; }
+            if (total >= opt.maxiter || res.status == SS_NOT_CONVERGED || (res.status == SS_BREAKDOWN && res.iters == 0)) {
+                status = res.status == SS_OK ? SS_NOT_CONVERGED : res.status;
+                break;
+            }
+            if (res.status == SS_OK) inner *= 0.1;
+            // a breakdown after progress restarts from x with a fresh shadow residual
+        }
+        return SS_OK;
+    };
     if (mixed) {
         // FP32 inner BiCGSTAB on r / ||r||, refined in FP64: x += ||r|| c
         STEP(su_zero(ctx, n, b));
@@ -707,34 +730,30 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
             total += res.iters;
             STEP(su_refine_update(ctx, n, x, scr, x32));
             if (res.status == SS_BREAKDOWN && res.iters == 0) { status = SS_BREAKDOWN; break; }
+            // an FP32 inner solve that cannot reach its tolerance within its cap
+            // has met the limit of FP32 for this system: the remaining
+            // iterations run in FP64 from the refined x
+            if (res.status == SS_NOT_CONVERGED && total < opt.maxiter) {
+                fp64_fallback = true;
+                break;
+            }
         }
         if (outer > 30) outer = 30;
         dev_free(ctx, r64);
         dev_free(ctx, b32);
         dev_free(ctx, x32);
+        if (fp64_fallback) {
+            STEP(su_lrho(ctx, Ap->m, x, 0, w_used, r0, d, tidx_d, y, scr, trace_d, &lr, nullptr));
+            if (lr <= opt.tol) status = SS_OK;
+            else STEP(fp64_passes());
+        }
     } else if (!power) {
         STEP(su_zero(ctx, n, b));
         double2 wb = make_double2(w_used, 0.0);
         SS_CUDA(ctx, cudaMemcpyAsync(b + r0, &wb, sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
         STEP(initial(x));
-        double inner = 0.5 * opt.tol;
         outer = 1;
-        for (int pass = 0; pass < 8; ++pass) {
-            int left = opt.maxiter - total;
-            if (krylov == SS_KRYLOV_GMRES)
-                STEP(gmres_dev(ctx, Ap->m, M, kw, b, x, inner, left, opt.restart, &res, nullptr, kaug));
-            else
-                STEP(bicgstab_dev(ctx, Ap->m, M, kw, b, x, inner, left, &res));
-            total += res.iters;
-            STEP(su_lrho(ctx, Ap->m, x, 0, w_used, r0, d, tidx_d, y, scr, trace_d, &lr, nullptr));
-            if (lr <= opt.tol) { status = SS_OK; break; }
-            if (total >= opt.maxiter || res.status == SS_NOT_CONVERGED || (res.status == SS_BREAKDOWN && res.iters == 0)) {
-                status = res.status == SS_OK ? SS_NOT_CONVERGED : res.status;
-                break;
-            }
-            if (res.status == SS_OK) inner *= 0.1;
-            // a breakdown after progress restarts from x with a fresh shadow residual
-        }
+        STEP(fp64_passes());
     } else {
         // x_0 random (SplitMix64 counters), ||x_0|| = 1; b holds x_k, x holds v
         if (opt.warm_start) STEP(initial(b));
@@ -779,6 +798,7 @@ extern "C" ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, con
     inf.status = status;
     inf.iters = total;
     inf.outer_iters = outer;
+    inf.fp64_fallback = fp64_fallback ? 1 : 0;
     inf.resid_Lrho = lr;
     inf.ms_setup = t1 - t0;
     inf.ms_solve = t2 - t1;

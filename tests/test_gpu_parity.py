@@ -413,6 +413,20 @@ def test_config3_optomechanics_mixed(ss):
     assert trace_distance(rho_d, ref.rho) <= 1e-9
 
 
+def test_config3_optomechanics_mixed_falls_back_to_fp64(ss):
+    """The second optomechanics system (seed 1) is beyond FP32 for the inner
+    solves: one stalls at its iteration cap, the remaining iterations run in
+    FP64 from the refined iterate (fp64_fallback), and the result reaches
+    ||L rho|| <= 1e-10 and agrees with the FP64 solve."""
+    s = optomechanics(seed=1)
+    rho_m, info_m = ss.steady_state(s.H, s.c_ops, precision="mixed", tol=1e-10)
+    assert info_m["status"] == 0 and info_m["resid_Lrho"] <= 1e-10
+    assert info_m["fp64_fallback"] == 1 and info_m["iters"] <= 1000
+    rho_d, info_d = ss.steady_state(s.H, s.c_ops, tol=1e-11)
+    assert info_d["status"] == 0 and info_d["fp64_fallback"] == 0
+    assert trace_distance(rho_m, rho_d) <= 1e-8
+
+
 @pytest.mark.parametrize("name", ["cavity_thermal", "kerr17", "jc8"])
 def test_mixed_single_system_small(ss, name):
     s = SMALL_SYSTEMS[name]()
