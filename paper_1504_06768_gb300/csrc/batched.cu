@@ -530,7 +530,8 @@ __device__ __forceinline__ void sf_row(const UnitRegs<float2>& cu, float2 rhs, c
 // warp loads its next unit while it solves the current one; nothing on the
 // path of a unit waits for a global load.  (Three units in registers, each
 // requested two unit solves ahead, put them in local memory: 1,514-1,525
-// against 1,964-1,967 solves/s on 608 JC40 systems.)
+// against 1,964-1,967 solves/s on 608 JC40 systems; bulk L2 prefetches of
+// the units three turns ahead, 2,100-2,114 against 2,159-2,175.)
 template <bool LOWER, int G>
 __device__ void cta_trsv_sfv(const PackedOp& P, const int32_t* __restrict__ ocol, const float2* __restrict__ oval,
                              const float2* __restrict__ inv, const float2* rhs, float2* x, const Ring& rg) {
@@ -1145,8 +1146,11 @@ __device__ double true_residual(const BatchSys& S, const double2* __restrict__ x
 // FP32 recursive residual has dropped by DELTA since the last replacement (or
 // every REFRESH iterations), it is replaced by the true FP64 residual
 // b - A x (reliable updating); the solve stops when the FP64 ||L rho||_2 <= tol.
-// A breakdown restarts the recurrence from the current x.
-constexpr double DELTA = 0.05;
+// A breakdown restarts the recurrence from the current x.  DELTA = 0.2 (JC40,
+// 608 systems: 116.8 iterations, 2,144-2,151 solves/s; 0.1: 121.3 and
+// 2,127; 0.05: 124.9 and 2,094-2,104; 0.3 and 0.5: 115.6 and 113.7
+// iterations, no faster).
+constexpr double DELTA = 0.2;
 constexpr int REFRESH = 50;
 
 __device__ void solve_mixed(BatchSys& S, const BatchParams& P, SmemPlan& sm, double* red) {
