@@ -167,8 +167,12 @@ __device__ __forceinline__ T wait_ready(const TrsvArgs<T>& a, int32_t c, T v, bo
     const T* xp = &a.x[c];
     const unsigned long long t0 = globaltimer_ns();
     int spins = 0;
+    // no back-off between reads: a value is read again as soon as the last
+    // read returns (backing off 32, then 256 ns measured 669-671 us in FP32
+    // and 1,304-1,309 us in FP64 per M^-1 r of the chain, against 598-599
+    // and 1,237-1,241 us)
     while (true) {
-        if (++spins > 8) __nanosleep(spins > 64 ? 256 : 32);
+        ++spins;
         v = __ldcv(xp);
         if (ready(v)) return v;
         if ((spins & 15) == 0 && (*(volatile int*)a.err != 0 || globaltimer_ns() - t0 > a.wait_ns)) {
