@@ -149,6 +149,29 @@ void build_pattern_host(Pattern& P, int use_rcm, const TuneChoice& tune) {
         lo += P.dpos[r] - prp[r];
         up += prp[r + 1] - P.dpos[r] - 1;
     }
+    // elimination schedule of iLU(0) on the permuted pattern: for the pivot
+    // at position t of row i (k = pcol[t] < i), the entries of row i after t
+    // that row k's upper part also holds, as (index in row i, position in row
+    // k), the same updates the IKJ elimination makes, in its order
+    P.ilu_ptr.assign((size_t)prp[n] + 1, 0);
+    P.ilu_tgt.clear();
+    P.ilu_src.clear();
+    for (int64_t r = 0; r < n; ++r) {
+        const int32_t rb = prp[r], re = prp[r + 1];
+        for (int32_t t = rb; t < re; ++t) {
+            P.ilu_ptr[t] = (int32_t)P.ilu_tgt.size();
+            if (t >= P.dpos[r]) continue;
+            const int32_t k = pcol[t];
+            for (int32_t u = P.dpos[k] + 1; u < prp[k + 1]; ++u) {
+                const auto it = std::lower_bound(pcol.begin() + t + 1, pcol.begin() + re, pcol[u]);
+                if (it != pcol.begin() + re && *it == pcol[u]) {
+                    P.ilu_tgt.push_back((int32_t)(it - pcol.begin()) - rb);
+                    P.ilu_src.push_back(u);
+                }
+            }
+        }
+    }
+    P.ilu_ptr[prp[n]] = (int32_t)P.ilu_tgt.size();
     std::vector<int32_t> uorder, uptr;
     P.n_levels = level_sets_host(n, prp.data(), pcol.data(), true, P.lorder, P.lptr);
     P.up_levels = level_sets_host(n, prp.data(), pcol.data(), false, uorder, uptr);
@@ -213,6 +236,9 @@ ss_status upload_pattern(ss_ctx ctx, Pattern& P) {
     SS_TRY(upload_vec(ctx, P.uunits, &P.up_units));
     SS_TRY(upload_vec(ctx, P.lptr, &P.lvl_ptr));
     SS_TRY(upload_vec(ctx, P.lorder, &P.lvl_rows));
+    SS_TRY(upload_vec(ctx, P.ilu_ptr, &P.ilu_ptr_d));
+    SS_TRY(upload_vec(ctx, P.ilu_tgt, &P.ilu_tgt_d));
+    SS_TRY(upload_vec(ctx, P.ilu_src, &P.ilu_src_d));
     SS_TRY(upload_vec(ctx, P.rp, &P.rp_d));
     SS_TRY(upload_vec(ctx, P.col, &P.col_d));
     return SS_OK;
@@ -223,6 +249,7 @@ ss_status upload_pattern(ss_ctx ctx, Pattern& P) {
 Pattern::~Pattern() {
     cudaSetDevice(device);
     void* ptrs[] = {rp_d, col_d, prp_d, pcol_d, map_d, perm_d, tidx_d, dpos_d, lo_units, up_units, lvl_ptr, lvl_rows,
+                    ilu_ptr_d, ilu_tgt_d, ilu_src_d,
                     lo.col, lo.src, lo.lvl, lo.meta, up.col, up.src, up.lvl, up.meta, pa.col, pa.src, pa.lvl, pa.meta};
     for (void* q : ptrs)
         if (q) cudaFreeAsync(q, 0);
@@ -513,6 +540,9 @@ ss_status wave_begin(BatchWave& w) {
         b.up.dinv = reinterpret_cast<void*>(take((size_t)P.up.nunits * (((32 / P.up.G) * inner + 15) & ~size_t(15))));
         b.lvl_ptr = P.lvl_ptr;
         b.lvl_rows = P.lvl_rows;
+        b.ilu_ptr = P.ilu_ptr_d;
+        b.ilu_tgt = P.ilu_tgt_d;
+        b.ilu_src = P.ilu_src_d;
         b.n_levels = P.n_levels;
         b.r0 = P.r0;
         b.w = blt.w[q];

@@ -41,6 +41,7 @@ struct Pattern {
     std::vector<int32_t> perm, iperm, tidx;
     int32_t r0 = 0;
     std::vector<int32_t> prp, pcol, map, dpos, lorder, lptr, lunits, uunits;
+    std::vector<int32_t> ilu_ptr, ilu_tgt, ilu_src;    // iLU(0) elimination schedule (see BatchSys)
     PackedHost hl, hu, ha;
     ss_status status = SS_OK;
     std::string error;
@@ -48,6 +49,7 @@ struct Pattern {
     int32_t *prp_d = nullptr, *pcol_d = nullptr, *map_d = nullptr;
     int32_t *perm_d = nullptr, *tidx_d = nullptr, *dpos_d = nullptr;
     int32_t *lo_units = nullptr, *up_units = nullptr, *lvl_ptr = nullptr, *lvl_rows = nullptr;
+    int32_t *ilu_ptr_d = nullptr, *ilu_tgt_d = nullptr, *ilu_src_d = nullptr;
     int32_t lo_nunits = 0, up_nunits = 0, lo_g = 1, up_g = 1, a_g = 1, n_levels = 0, up_levels = 0;
     PackedDev lo, up, pa;
     int device = 0;

@@ -932,31 +932,104 @@ __device__ __forceinline__ int32_t find_col_b(const int32_t* __restrict__ col, i
     return -1;
 }
 
-__device__ bool cta_ilu0(const BatchSys& S, bool mixed) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// IKJ elimination restricted to the pattern, level by level, from the
+// elimination schedule (no column search): a row's pivots in ascending
+// order, l_ik = a_ik / u_kk (as a_ik times the stored 1 / u_kk), then
+// a_ij -= l_ik u_kj for the entries the schedule lists.  Rows of a level go
+// to groups of ILU_GS lanes (two rows per warp at a time); a group stages
+// its row, the 1 / u_kk of its pivots and the u_kj its updates read in its
+// share of the shared memory (free until the solve starts), so the pivot
+// chain runs on shared memory; a row too long for the share is eliminated
+// in global memory in the same order.  When a row is done its 1 / u_ii is
+// stored for the rows of later levels.
+constexpr int ILU_GS = 16;
+constexpr int ILU_GROUPS = BT / ILU_GS;
+
+// stage: the shared memory may be used (not while bulk copies of an abandoned
+// ring might still land in it).
+__device__ bool cta_ilu0(const BatchSys& S, bool mixed, unsigned char* smem, int smem_bytes, bool stage) {
+    const int sub = threadIdx.x % ILU_GS, grp = threadIdx.x / ILU_GS;
+    const unsigned gmask = ILU_GS == 32 ? FULLM : (((1u << ILU_GS) - 1u) << ((threadIdx.x & 31) & ~(ILU_GS - 1)));
     const int32_t nnz = S.f_rp[S.n];
     double2* val = S.f_val;
     for (int32_t k = threadIdx.x; k < nnz; k += BT) val[k] = S.a_val[k];
     __syncthreads();
+    // this group's share: row values, 1 / u_kk per pivot, pivot ranges of the
+    // schedule (rebased to the row), and per update its target and u_kj
+    const int region = (smem_bytes / ILU_GROUPS) & ~15;
+    unsigned char* base = smem + (size_t)grp * region;
     for (int32_t l = 0; l < S.n_levels; ++l) {
-        for (int32_t q = S.lvl_ptr[l] + warp; q < S.lvl_ptr[l + 1]; q += NW) {
-            const int32_t i = S.lvl_rows[q];
-            const int32_t re = S.f_rp[i + 1], di = S.f_dpos[i];
-            for (int32_t t = S.f_rp[i]; t < di; ++t) {
-                const int32_t k = S.f_col[t];
-                double2 f = make_double2(0.0, 0.0);
-                if (lane == 0) {
-                    f = cdiv(val[t], val[S.f_dpos[k]]);
-                    val[t] = f;
+        const int32_t lb = S.lvl_ptr[l], le = S.lvl_ptr[l + 1];
+        // every group of a warp runs the same number of rounds (the warp's
+        // groups meet at __syncwarp), idle groups with no row
+        const int32_t rounds = (le - lb + ILU_GROUPS - 1) / ILU_GROUPS;
+        for (int32_t rd = 0; rd < rounds; ++rd) {
+            const int32_t q = lb + rd * ILU_GROUPS + grp;
+            const bool have = q < le;
+            int32_t i = 0, rb = 0, re = 0, di = 0, ub = 0, ue = 0;
+            if (have) {
+                i = S.lvl_rows[q];
+                rb = S.f_rp[i];
+                re = S.f_rp[i + 1];
+                di = S.f_dpos[i];
+                ub = S.ilu_ptr[rb];
+                ue = S.ilu_ptr[di];
+            }
+            const int32_t len = re - rb, npiv = di - rb, np = ue - ub;
+            const size_t need = (size_t)len * 32 + (size_t)(npiv + 1) * 4 + (size_t)np * 20 + 64;
+            const bool staged = stage && have && need <= (size_t)region;
+            double2* rv = reinterpret_cast<double2*>(base);                 // len
+            double2* pinv = rv + len;                                        // npiv
+            double2* uval = pinv + npiv;                                     // np
+            int32_t* tptr = reinterpret_cast<int32_t*>(uval + np);           // npiv + 1
+            int32_t* utgt = tptr + npiv + 1;                                 // np
+            if (staged) {
+                for (int32_t e = sub; e < len; e += ILU_GS) {
+                    rv[e] = val[rb + e];
+                    if (e < npiv) pinv[e] = S.f_inv[S.f_col[rb + e]];
                 }
-                f.x = __shfl_sync(FULLM, f.x, 0);
-                f.y = __shfl_sync(FULLM, f.y, 0);
-                for (int32_t u = S.f_dpos[k] + 1 + lane; u < S.f_rp[k + 1]; u += 32) {
-                    const int32_t pos = find_col_b(S.f_col, t + 1, re, S.f_col[u]);
-                    if (pos >= 0) val[pos] = csub(val[pos], cmul(f, val[u]));
+                for (int32_t e = sub; e <= npiv; e += ILU_GS) tptr[e] = S.ilu_ptr[rb + e] - ub;
+                for (int32_t p = sub; p < np; p += ILU_GS) {
+                    utgt[p] = S.ilu_tgt[ub + p];
+                    uval[p] = val[S.ilu_src[ub + p]];
+                }
+            }
+            __syncwarp();
+            const int32_t pmax = __reduce_max_sync(FULLM, have ? npiv : 0);
+            for (int32_t t = 0; t < pmax; ++t) {
+                // every lane of the group reads a_it; l_it replaces it after the
+                // warp has met (the updates only touch entries after t)
+                double2 f = make_double2(0.0, 0.0);
+                if (t < npiv) {
+                    if (staged) {
+                        f = cmul(rv[t], pinv[t]);
+                        for (int32_t p = tptr[t] + sub; p < tptr[t + 1]; p += ILU_GS) {
+                            const int32_t tg = utgt[p];
+                            if (tg < len) rv[tg] = csub(rv[tg], cmul(f, uval[p]));
+                        }
+                    } else {
+                        f = cmul(val[rb + t], S.f_inv[S.f_col[rb + t]]);
+                        for (int32_t p = S.ilu_ptr[rb + t] + sub; p < S.ilu_ptr[rb + t + 1]; p += ILU_GS) {
+                            const int32_t tg = rb + S.ilu_tgt[p];
+                            val[tg] = csub(val[tg], cmul(f, val[S.ilu_src[p]]));
+                        }
+                    }
                 }
                 __syncwarp();
+                if (t < npiv && sub == 0) {
+                    if (staged) rv[t] = f;
+                    else val[rb + t] = f;
+                }
             }
+            __syncwarp();
+            if (staged)
+                for (int32_t e = sub; e < len; e += ILU_GS) val[rb + e] = rv[e];
+            __syncwarp(gmask);
+            if (have && sub == 0) {
+                const double2 dg = staged ? rv[npiv] : val[di];
+                S.f_inv[i] = (dg.x == 0.0 && dg.y == 0.0) ? make_double2(0.0, 0.0) : cdiv(make_double2(1.0, 0.0), dg);
+            }
+            __syncwarp();
         }
         __syncthreads();
     }
@@ -964,11 +1037,12 @@ __device__ bool cta_ilu0(const BatchSys& S, bool mixed) {
     if (threadIdx.x == 0) zero_pivot = 0;
     __syncthreads();
     for (int32_t i = threadIdx.x; i < S.n; i += BT) {
-        double2 dg = val[S.f_dpos[i]];
+        const double2 dg = val[S.f_dpos[i]];
         if (dg.x == 0.0 && dg.y == 0.0) zero_pivot = 1;
-        double2 r = cdiv(make_double2(1.0, 0.0), dg);
-        S.f_inv[i] = r;
-        if (mixed) S.f_inv32[i] = make_float2((float)r.x, (float)r.y);
+        if (mixed) {
+            const double2 r = S.f_inv[i];
+            S.f_inv32[i] = make_float2((float)r.x, (float)r.y);
+        }
     }
     if (mixed) {
         for (int32_t k = threadIdx.x; k < nnz; k += BT) {
@@ -1428,7 +1502,7 @@ __global__ void __launch_bounds__(BT, BATCH_BLOCKS_PER_SM) batched_solver(BatchS
         }
         __syncthreads();
         bool ok = true;
-        if (S.factor_on_device) ok = cta_ilu0(S, MIXED);
+        if (S.factor_on_device) ok = cta_ilu0(S, MIXED, smem, P.smem_bytes, *(volatile int*)&ring_abort == 0);
         if (!ok) {
             if (threadIdx.x == 0) {
                 sys[k].status = SS_ZERO_PIVOT;
@@ -1633,6 +1707,7 @@ ss_status batch_launch(ss_ctx ctx, BatchSys* dsys, int nsys, BatchParams p, cons
     const size_t cap = (size_t)optin > fa.sharedSizeBytes + 256 ? (size_t)optin - fa.sharedSizeBytes - 256 : 0;
     const size_t smem = p.mixed ? choose_plan<float2>(shapes, cap, p) : choose_plan<double2>(shapes, cap, p);
     if (smem > cap) return set_error(ctx, SS_ERR_UNSUPPORTED, "system too large for the per-system solver's shared memory");
+    p.smem_bytes = (int)smem;
     const int grid = std::max(1, std::min(nsys, BATCH_BLOCKS_PER_SM * (ctx->num_sms > 0 ? ctx->num_sms : 1)));
     if (p.mixed) {
         SS_CUDA(ctx, cudaFuncSetAttribute(batched_solver<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

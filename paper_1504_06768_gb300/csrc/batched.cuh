@@ -54,6 +54,12 @@ struct BatchSys {
     const int32_t* lvl_ptr;     // lower level boundaries in lvl_rows (factorisation schedule)
     const int32_t* lvl_rows;
     int32_t n_levels;
+    // elimination schedule: the pivot at CSR position t updates the entries
+    // ilu_tgt[p] (index within its row) with the values at ilu_src[p] (CSR
+    // positions in the pivot's row), p in [ilu_ptr[t], ilu_ptr[t + 1])
+    const int32_t* ilu_ptr;
+    const int32_t* ilu_tgt;
+    const int32_t* ilu_src;
     // right-hand side / trace
     int32_t r0;                 // permuted position of row 0
     double w;                   // weight of the trace row (0: shifted system)
@@ -88,6 +94,7 @@ struct BatchParams {
     int ring_slot_bytes;
     int lvl_smem;               // level boundaries copied to shared memory
     int pbuf_smem;              // mixed precision: p^ kept in shared memory
+    int smem_bytes;             // dynamic shared memory of a block (staging of the factorisation's rows)
     int sf;                     // mixed precision: triangular solves without level barriers (values as flags)
 };
 
