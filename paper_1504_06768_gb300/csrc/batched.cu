@@ -936,13 +936,15 @@ __device__ __forceinline__ int32_t find_col_b(const int32_t* __restrict__ col, i
 // elimination schedule (no column search): a row's pivots in ascending
 // order, l_ik = a_ik / u_kk (as a_ik times the stored 1 / u_kk), then
 // a_ij -= l_ik u_kj for the entries the schedule lists.  Rows of a level go
-// to groups of ILU_GS lanes (two rows per warp at a time); a group stages
+// to groups of ILU_GS lanes (32 / ILU_GS rows per warp at a time); a group stages
 // its row, the 1 / u_kk of its pivots and the u_kj its updates read in its
 // share of the shared memory (free until the solve starts), so the pivot
 // chain runs on shared memory; a row too long for the share is eliminated
 // in global memory in the same order.  When a row is done its 1 / u_ii is
-// stored for the rows of later levels.
-constexpr int ILU_GS = 16;
+// stored for the rows of later levels.  Four lanes per row (JC40, 608
+// systems: 2,853-2,879 solves/s; 16 lanes 2,738-2,762, 8 lanes 2,818, 2
+// lanes 2,829-2,848, one lane 2,765-2,782).
+constexpr int ILU_GS = 4;
 constexpr int ILU_GROUPS = BT / ILU_GS;
 
 // stage: the shared memory may be used (not while bulk copies of an abandoned
