@@ -290,6 +290,21 @@ ss_status ss_rcm_order_host(int64_t n, const int32_t* row_ptr, const int32_t* co
 ss_status ss_level_sets_host(int64_t n, const int32_t* row_ptr, const int32_t* col, int lower,
                              int32_t* order_out, int32_t* level_ptr_out, int32_t* n_levels_out);
 
+/* Elimination schedule of iLU(0) (section "Iterative solvers": incomplete
+ * LU without fill, by IKJ elimination restricted to the pattern) for a CSR
+ * pattern with ascending columns and every diagonal entry stored; the
+ * batched solver factors each system from the schedule of its pattern.  For
+ * the pivot at CSR position t of row i (k = col[t] < i) the updates are
+ * the pairs p in [ptr_out[t], ptr_out[t + 1]): a[row_ptr[i] + tgt_out[p]] -=
+ * l * a[src_out[p]] with l = a[t] / u_kk, in the order listed, after the
+ * pivots before t; positions that are not pivots have empty ranges.
+ * *count_out receives the number of pairs; when it exceeds `capacity`
+ * nothing else is written and SS_ERR_INVALID is returned (call again with
+ * enough room: ptr_out row_ptr[n] + 1 entries, tgt_out and src_out count
+ * entries).  SS_ZERO_PIVOT: a diagonal entry is missing. */
+ss_status ss_ilu0_schedule_host(int64_t n, const int32_t* row_ptr, const int32_t* col, int64_t capacity,
+                                int32_t* ptr_out, int32_t* tgt_out, int32_t* src_out, int64_t* count_out);
+
 /* ILUT(drop_tol, fill_factor) without pivoting (section "Iterative
  * solvers"; the rules of ilu_factor with SS_PRECOND_ILUT) on a complex CSR
  * matrix (val: 2 * nnz doubles, interleaved).  Output: the combined factors

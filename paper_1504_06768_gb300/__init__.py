@@ -151,6 +151,28 @@ def level_sets_host(A, lower: bool = True):
     return order, ptr[:nl.value + 1].copy()
 
 
+def ilu0_schedule_host(A):
+    """The iLU(0) elimination schedule of A's pattern on the host (no GPU):
+    (ptr, tgt, src) over A's CSR with sorted columns, as
+    ss_ilu0_schedule_host describes them."""
+    h = _CsrHost(A)
+    n = h.view.n_rows
+    lib = B.load()
+    cnt = C.c_int64(-1)
+    ptr = np.empty(int(h.rp[-1]) + 1, dtype=np.int32)
+    st = lib.ss_ilu0_schedule_host(n, h.rp.ctypes.data, h.col.ctypes.data, 0, ptr.ctypes.data, None, None,
+                                   C.byref(cnt))
+    if st == B.SS_ZERO_PIVOT:
+        raise SolverError(st, "ss_ilu0_schedule_host: a diagonal entry is missing")
+    if cnt.value < 0:
+        _host_status(st, "ss_ilu0_schedule_host")
+    tgt = np.empty(max(cnt.value, 1), dtype=np.int32)
+    src = np.empty(max(cnt.value, 1), dtype=np.int32)
+    _host_status(lib.ss_ilu0_schedule_host(n, h.rp.ctypes.data, h.col.ctypes.data, cnt.value, ptr.ctypes.data,
+                                           tgt.ctypes.data, src.ctypes.data, C.byref(cnt)), "ss_ilu0_schedule_host")
+    return ptr, tgt[:cnt.value].copy(), src[:cnt.value].copy()
+
+
 def ilut_host(A, drop_tol: float = 1e-4, fill_factor: float = 10.0):
     """ILUT factors of A computed on the host (no GPU), as a scipy CSR matrix
     of the combined factors (strict lower = L with unit diagonal, rest = U)."""

@@ -109,6 +109,7 @@ _SIGNATURES = {
                                C.POINTER(C.c_int), _DP]),
     "ss_rcm_order_host": (C.c_int, [C.c_int64, _P, _P, _P]),
     "ss_level_sets_host": (C.c_int, [C.c_int64, _P, _P, C.c_int, _P, _P, C.POINTER(C.c_int32)]),
+    "ss_ilu0_schedule_host": (C.c_int, [C.c_int64, _P, _P, C.c_int64, _P, _P, _P, _I64P]),
     "ss_ilut_host": (C.c_int, [C.c_int64, _P, _P, _P, C.c_double, C.c_double, C.c_int64, _P, _P, _P,
                                _I64P, _I64P]),
     "ss_mbm_host": (C.c_int, [C.c_int64, _P, _P, _P, _P, _I64P]),

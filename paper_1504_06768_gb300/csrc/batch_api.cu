@@ -149,29 +149,9 @@ void build_pattern_host(Pattern& P, int use_rcm, const TuneChoice& tune) {
         lo += P.dpos[r] - prp[r];
         up += prp[r + 1] - P.dpos[r] - 1;
     }
-    // elimination schedule of iLU(0) on the permuted pattern: for the pivot
-    // at position t of row i (k = pcol[t] < i), the entries of row i after t
-    // that row k's upper part also holds, as (index in row i, position in row
-    // k), the same updates the IKJ elimination makes, in its order
-    P.ilu_ptr.assign((size_t)prp[n] + 1, 0);
-    P.ilu_tgt.clear();
-    P.ilu_src.clear();
-    for (int64_t r = 0; r < n; ++r) {
-        const int32_t rb = prp[r], re = prp[r + 1];
-        for (int32_t t = rb; t < re; ++t) {
-            P.ilu_ptr[t] = (int32_t)P.ilu_tgt.size();
-            if (t >= P.dpos[r]) continue;
-            const int32_t k = pcol[t];
-            for (int32_t u = P.dpos[k] + 1; u < prp[k + 1]; ++u) {
-                const auto it = std::lower_bound(pcol.begin() + t + 1, pcol.begin() + re, pcol[u]);
-                if (it != pcol.begin() + re && *it == pcol[u]) {
-                    P.ilu_tgt.push_back((int32_t)(it - pcol.begin()) - rb);
-                    P.ilu_src.push_back(u);
-                }
-            }
-        }
-    }
-    P.ilu_ptr[prp[n]] = (int32_t)P.ilu_tgt.size();
+    // elimination schedule of iLU(0) on the permuted pattern (the updates of
+    // the IKJ elimination, in its order; shared by the pattern's systems)
+    ilu0_schedule_host(n, prp.data(), pcol.data(), P.dpos.data(), P.ilu_ptr, P.ilu_tgt, P.ilu_src);
     std::vector<int32_t> uorder, uptr;
     P.n_levels = level_sets_host(n, prp.data(), pcol.data(), true, P.lorder, P.lptr);
     P.up_levels = level_sets_host(n, prp.data(), pcol.data(), false, uorder, uptr);

@@ -26,6 +26,19 @@ int32_t level_sets_host(int64_t n, const int32_t* row_ptr, const int32_t* col, b
 void level_units_host(const std::vector<int32_t>& order, const std::vector<int32_t>& level_ptr, int R,
                       std::vector<int32_t>& units);
 
+// Elimination schedule of iLU(0) (IKJ elimination restricted to the pattern
+// of an n x n CSR with ascending columns; dpos[i]: position of row i's
+// diagonal).  For the pivot at position t of row i (k = col[t] < i): the
+// entries j > t of row i whose column row k's upper part (after its
+// diagonal) also holds, as tgt = j - row_ptr[i] and src = the position in
+// row k, at tgt/src[ptr[t] .. ptr[t + 1]) in ascending order of the row k
+// position; ptr has row_ptr[n] + 1 entries (empty ranges for non-pivots).
+// The elimination is: for each row, for each pivot t in ascending order,
+// l = a[t] / a[dpos[k]], a[t] = l, a[row_ptr[i] + tgt] -= l a[src] for the
+// listed pairs.
+void ilu0_schedule_host(int64_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* dpos,
+                        std::vector<int32_t>& ptr, std::vector<int32_t>& tgt, std::vector<int32_t>& src);
+
 // ILUT(drop_tol, fill_factor) without pivoting on an n x n CSR matrix with
 // interleaved complex values.  Output: combined factors (strict lower part =
 // L with unit diagonal, diagonal and upper part = U), sorted columns.

@@ -43,6 +43,28 @@ extern "C" ss_status ss_level_sets_host(int64_t n, const int32_t* row_ptr, const
     return SS_OK;
 }
 
+extern "C" ss_status ss_ilu0_schedule_host(int64_t n, const int32_t* row_ptr, const int32_t* col, int64_t capacity,
+                                           int32_t* ptr_out, int32_t* tgt_out, int32_t* src_out, int64_t* count_out) {
+    if (!count_out || !csr_ok(n, row_ptr, col)) return SS_ERR_INVALID;
+    std::vector<int32_t> dpos((size_t)n, -1);
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t t = row_ptr[i]; t < row_ptr[i + 1]; ++t)
+            if (col[t] == i) dpos[i] = t;
+    for (int64_t i = 0; i < n; ++i)
+        if (dpos[i] < 0) return SS_ZERO_PIVOT;
+    std::vector<int32_t> ptr, tgt, src;
+    ilu0_schedule_host(n, row_ptr, col, dpos.data(), ptr, tgt, src);
+    const int64_t count = (int64_t)tgt.size();
+    *count_out = count;
+    if (capacity < count || !ptr_out || (count > 0 && (!tgt_out || !src_out))) return SS_ERR_INVALID;
+    std::memcpy(ptr_out, ptr.data(), sizeof(int32_t) * ptr.size());
+    if (count > 0) {
+        std::memcpy(tgt_out, tgt.data(), sizeof(int32_t) * (size_t)count);
+        std::memcpy(src_out, src.data(), sizeof(int32_t) * (size_t)count);
+    }
+    return SS_OK;
+}
+
 extern "C" ss_status ss_ilut_host(int64_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
                                   double drop_tol, double fill_factor, int64_t capacity, int32_t* f_row_ptr,
                                   int32_t* f_col, double* f_val, int64_t* nnz_out, int64_t* zero_pivot_row) {

@@ -114,3 +114,31 @@ void level_units_host(const std::vector<int32_t>& order, const std::vector<int32
             for (int g = 0; g < R; ++g) units.push_back(a + g < level_ptr[l + 1] ? order[a + g] : -1);
     }
 }
+
+// iLU(0) elimination schedule (section "Iterative solvers": incomplete LU
+// without fill): for every pivot position t of row i, the entries of row i
+// after t that the pivot row's upper part also holds.  Columns are sorted,
+// so each match is a binary search in row i's remaining columns.
+void ilu0_schedule_host(int64_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* dpos,
+                        std::vector<int32_t>& ptr, std::vector<int32_t>& tgt, std::vector<int32_t>& src) {
+    const int32_t nnz = n > 0 ? row_ptr[n] : 0;
+    ptr.assign((size_t)nnz + 1, 0);
+    tgt.clear();
+    src.clear();
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t rb = row_ptr[i], re = row_ptr[i + 1];
+        for (int32_t t = rb; t < re; ++t) {
+            ptr[t] = (int32_t)tgt.size();
+            if (t >= dpos[i]) continue;
+            const int32_t k = col[t];
+            for (int32_t u = dpos[k] + 1; u < row_ptr[k + 1]; ++u) {
+                const int32_t* it = std::lower_bound(col + t + 1, col + re, col[u]);
+                if (it != col + re && *it == col[u]) {
+                    tgt.push_back((int32_t)(it - col) - rb);
+                    src.push_back(u);
+                }
+            }
+        }
+    }
+    ptr[nnz] = (int32_t)tgt.size();
+}

@@ -101,6 +101,48 @@ def test_ilut_host_matches_oracle(ss, name, drop, fill):
     assert np.max(np.abs(got.data - ref.data)) <= 1e-12 * np.max(np.abs(ref.data))
 
 
+@pytest.mark.parametrize("name", sorted(SYSTEMS))
+def test_ilu0_schedule_reproduces_the_oracles_ilu0(ss, name):
+    """The batched solver factors each system from its pattern's elimination
+    schedule.  Eliminating with the schedule alone (for each row, each pivot
+    in ascending order: l = a_it / u_kk, then a_ij -= l u_kj for the listed
+    pairs) gives the oracle's iLU(0) of the RCM-ordered trace-row system."""
+    A = _modified(SYSTEMS[name]())
+    Ap = sp.csr_matrix(permute_symmetric(A, rcm_order(A)))
+    Ap.sort_indices()
+    ptr, tgt, src = ss.ilu0_schedule_host(Ap)
+    rp, col = Ap.indptr, Ap.indices
+    n = Ap.shape[0]
+    dpos = np.array([rp[i] + int(np.searchsorted(col[rp[i]:rp[i + 1]], i)) for i in range(n)])
+    a = [complex(v) for v in Ap.data]
+    for i in range(n):
+        for t in range(rp[i], dpos[i]):
+            k = col[t]
+            a[t] = a[t] / a[dpos[k]]
+            for p in range(ptr[t], ptr[t + 1]):
+                j = rp[i] + tgt[p]
+                assert t < j < rp[i + 1] and dpos[k] < src[p] < rp[k + 1] and col[j] == col[src[p]]
+                a[j] = a[j] - a[t] * a[src[p]]
+    ref = oilu.ilu0(Ap)
+    ref.sort_indices()
+    assert np.array_equal(ref.indptr, rp) and np.array_equal(ref.indices, col)
+    got = np.array(a)
+    assert np.max(np.abs(got - ref.data)) <= 1e-13 * np.max(np.abs(ref.data))
+    # positions that are not pivots have empty ranges
+    pivots = np.zeros(rp[-1], dtype=bool)
+    for i in range(n):
+        pivots[rp[i]:dpos[i]] = True
+    assert np.all(np.diff(ptr)[~pivots] == 0)
+
+
+def test_ilu0_schedule_host_rejects_missing_diagonal(ss):
+    A = sp.csr_matrix(np.array([[0.0, 1.0], [1.0, 1.0]], dtype=complex))
+    A.eliminate_zeros()
+    with pytest.raises(ss.SolverError) as e:
+        ss.ilu0_schedule_host(A)
+    assert e.value.status == 5
+
+
 def test_ilut_host_zero_pivot(ss):
     A = sp.csr_matrix(np.array([[0.0, 1.0], [1.0, 1.0]], dtype=complex))
     with pytest.raises(ss.SolverError) as e:
