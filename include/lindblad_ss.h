@@ -380,8 +380,11 @@ ss_status steady_state(ss_ctx ctx, const ss_csr_view* H, int n_c, const ss_csr_v
  * iterations on r/||r|| refined in FP64 until ||L rho||_2 <= tol) and the
  * finalisation.  Systems sharing a sparsity pattern share one RCM ordering and
  * level schedule.  Other systems and options go through steady_state() one at
- * a time.  Returns SS_OK when every system converged, otherwise the status of
- * a failing system (each info holds its own status). */
+ * a time.  Host results (rho_on_device == 0) pass through pinned host memory
+ * that the context keeps for later calls (grown to the largest batch's
+ * results, freed by ss_ctx_destroy; pageable copies if it cannot be had).
+ * Returns SS_OK when every system converged, otherwise the status of a
+ * failing system (each info holds its own status). */
 ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_view* H, const int* n_c,
                                const ss_csr_view* const* c_ops, const ss_options* opt,
                                double* const* rho_out, int rho_on_device, ss_info* infos);

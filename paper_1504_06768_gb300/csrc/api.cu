@@ -121,6 +121,7 @@ extern "C" ss_status ss_ctx_destroy(ss_ctx ctx) {
     if (!ctx) return SS_ERR_INVALID;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->host_stage) cudaFreeHost(ctx->host_stage);
     delete ctx;
     return SS_OK;
 }

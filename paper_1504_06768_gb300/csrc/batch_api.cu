@@ -637,9 +637,21 @@ ss_status wave_end(BatchWave& w, ss_info* infos) {
             const size_t hs_bytes = (ns * sizeof(BatchSys) + 255) & ~size_t(255);
             std::memcpy(w.hs.data(), base, sizeof(BatchSys) * ns);
             std::memcpy(&herr, base + hs_bytes, sizeof(int));
-            if (!w.rho_on_device)
-                for (size_t q = 0; q < ns; ++q)
-                    std::memcpy(w.rho_out[q], base + w.stage_off[q], sizeof(double2) * w.blt.n[q]);
+            if (!w.rho_on_device) {
+                // large results are copied out by several host threads
+                size_t total = 0;
+                for (size_t q = 0; q < ns; ++q) total += sizeof(double2) * w.blt.n[q];
+                const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+                const size_t nt = std::min<size_t>({ns, (size_t)std::min(8u, hw), total / ((size_t)4 << 20) + 1});
+                auto copy = [&](size_t t) {
+                    for (size_t q = t; q < ns; q += nt)
+                        std::memcpy(w.rho_out[q], base + w.stage_off[q], sizeof(double2) * w.blt.n[q]);
+                };
+                std::vector<std::thread> th;
+                for (size_t t = 1; t < nt; ++t) th.emplace_back(copy, t);
+                copy(0);
+                for (std::thread& x : th) x.join();
+            }
         } else {
             e = cudaMemcpyAsync(w.hs.data(), w.dsys, sizeof(BatchSys) * ns, cudaMemcpyDeviceToHost, ctx->stream);
             if (e == cudaSuccess)
@@ -839,6 +851,25 @@ extern "C" ss_status steady_state_batched(ss_ctx ctx, int n_sys, const ss_csr_vi
         w.rho_out.push_back(rho_out[k]);
     }
     if (opt.autotune) SS_TRY(autotune_batch(ctx, w, &w.tune));
+    if (!rho_on_device) {
+        // host results come back through the context's pinned buffer: one
+        // asynchronous copy per system there, then host copies (pageable
+        // destinations would make every device copy a staged, blocking one)
+        const size_t need = wave_pinned_bytes(w);
+        if (ctx->host_stage_bytes < need) {
+            if (ctx->host_stage) cudaFreeHost(ctx->host_stage);
+            ctx->host_stage = nullptr;
+            ctx->host_stage_bytes = 0;
+            if (cudaHostAlloc(&ctx->host_stage, need, cudaHostAllocDefault) == cudaSuccess)
+                ctx->host_stage_bytes = need;
+            else
+                cudaGetLastError();          // no pinned memory: pageable copies instead
+        }
+        if (ctx->host_stage) {
+            w.stage_pinned = true;
+            w.stage = static_cast<double2*>(ctx->host_stage);
+        }
+    }
     SS_TRY(wave_begin(w));
     std::vector<ss_info> winf(fastidx.size());
     ss_status st = wave_end(w, winf.data());

@@ -95,6 +95,10 @@ struct ss_ctx_s {
     // the batched solver's autotuned choices (lanes-per-row shifts, staging
     // flip) per batch shape, kept for later batches of the same shape
     std::map<unsigned long long, std::array<int, 4>> tune_table;
+    // pinned host memory through which steady_state_batched returns host
+    // results (grown on demand, kept until the context is destroyed)
+    void* host_stage = nullptr;
+    size_t host_stage_bytes = 0;
 };
 
 struct ss_mat_s {
