@@ -146,7 +146,9 @@ typedef struct {
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  The stream is
- * borrowed and must outlive the context. */
+ * borrowed and must outlive the context.  The library allocates device
+ * memory from one memory pool per device, shared by its contexts, that
+ * keeps freed blocks for later allocations until the process exits. */
 ss_status ss_ctx_create(int device, void* cuda_stream, ss_ctx* out);
 ss_status ss_ctx_destroy(ss_ctx ctx);
 /* Replace the stream used by later calls. */

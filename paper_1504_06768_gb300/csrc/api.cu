@@ -107,6 +107,7 @@ extern "C" ss_status ss_ctx_create(int device, void* cuda_stream, ss_ctx* out) {
     c->device = device;
     c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    c->pool = device_pool(device);
     // the allocation-free entry point's workspace is loaded here, not in its first call
     const ss_status st = noalloc_prepare(c);
     if (st != SS_OK) {

@@ -99,6 +99,9 @@ struct ss_ctx_s {
     // results (grown on demand, kept until the context is destroyed)
     void* host_stage = nullptr;
     size_t host_stage_bytes = 0;
+    // device memory pool of the context's device (see device_pool; null: the
+    // device's default pool)
+    cudaMemPool_t pool = nullptr;
 };
 
 struct ss_mat_s {
@@ -182,6 +185,12 @@ struct ProfScope {
 // ------------------------------------------------------------ allocation
 
 ss_status dev_alloc(ss_ctx ctx, void** p, size_t bytes);
+// The process-wide memory pool of a device from which the library's
+// contexts allocate: freed blocks stay in it for later allocations instead
+// of going back to the driver at every synchronisation.  Created on first
+// use, never destroyed (memory freed after its context is gone still returns
+// to a live pool).  Null when the device cannot make one.
+cudaMemPool_t device_pool(int device);
 void dev_free(ss_ctx ctx, void* p);
 void dev_free_nostream(void* p);
 template <class T> ss_status dev_alloc_n(ss_ctx ctx, T** p, size_t n) {

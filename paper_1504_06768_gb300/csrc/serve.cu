@@ -258,6 +258,7 @@ std::unique_ptr<ss_ctx_s> make_ctx(int device, int num_sms, bool high) {
         cudaGetLastError();
         return nullptr;
     }
+    c->pool = device_pool(device);
     return c;
 }
 

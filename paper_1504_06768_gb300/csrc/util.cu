@@ -3,6 +3,9 @@
 #include <cstdio>
 #include <cstring>
 
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 
 ss_status set_error(ss_ctx ctx, ss_status st, const std::string& msg) {
@@ -21,13 +24,38 @@ ss_status cuda_check(ss_ctx ctx, cudaError_t e, const char* what) {
 ss_status dev_alloc(ss_ctx ctx, void** p, size_t bytes) {
     *p = nullptr;
     ss_count_alloc();
-    cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+    cudaError_t e = ctx->pool ? cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream)
+                              : cudaMallocAsync(p, bytes, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return set_error(ctx, SS_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
     }
     return SS_OK;
+}
+
+cudaMemPool_t device_pool(int device) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = pools.find(device);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+        // keep every freed block: a batched step allocates and frees the same
+        // gigabytes each time
+        uint64_t keep = UINT64_MAX;
+        if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) cudaGetLastError();
+    } else {
+        cudaGetLastError();
+        pool = nullptr;
+    }
+    pools[device] = pool;
+    return pool;
 }
 
 void dev_free(ss_ctx ctx, void* p) {
