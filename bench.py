@@ -636,7 +636,8 @@ def configs_measure(ss):
       in one steady_state_batched call, mixed and FP64, against the same 512
       solved one at a time by steady_state in FP64 (the plain GPU path);
     * optomechanics 10 x 40 (n = 160,000) by steady_state, mixed and FP64;
-    * JC40 with ILUT(1e-4, 10) by BiCGSTAB and by GMRES(30) (FP64)."""
+    * JC40 with ILUT(1e-4, 10) by BiCGSTAB and by GMRES(30) (FP64);
+    * one JC40 system through the single-system path (single_system_measure)."""
     import numpy as np
     from workloads import jaynes_cummings_rwa, kerr_sweep, optomechanics
     res = {}
@@ -704,7 +705,28 @@ def configs_measure(ss):
             "converged": sum(o[1]["status"] == 0 for o in out), "nnz_factors": out[0][1]["nnz_factors"],
             "max_resid_Lrho": max(o[1]["resid_Lrho"] for o in out)}
     res["jc40_ilut"] = c2
+    res["jc40_single"] = single_system_measure(ss, jaynes_cummings_rwa(seed=0))
     return res
+
+
+def single_system_measure(ss, s):
+    """One JC40 system (n = 6400) through steady_state, one call at a time:
+    the banded direct LU (FP64) and iLU(0)-preconditioned BiCGSTAB in FP64
+    and mixed precision.  Each is called once untimed, then timed as the wall
+    time of a complete call; a failure is recorded, not raised."""
+    out = {"system": "JC40, seed 0", "n": s.d * s.d, "tol": TOL}
+    for meth, prec in (("direct", "fp64"), ("iterative-bicgstab", "fp64"), ("iterative-bicgstab", "mixed")):
+        key = f"{meth}_{prec}"
+        try:
+            ss.steady_state(s.H, s.c_ops, method=meth, precision=prec, tol=TOL, raise_on_failure=False)
+            t0 = time.perf_counter()
+            _, info = ss.steady_state(s.H, s.c_ops, method=meth, precision=prec, tol=TOL, raise_on_failure=False)
+            out[key] = {"s_per_solve": time.perf_counter() - t0, "status": info["status"],
+                        "resid_Lrho": info["resid_Lrho"], "iters": info["iters"],
+                        "ms_setup": info["ms_setup"], "ms_solve": info["ms_solve"]}
+        except Exception as e:                      # a measurement block never ends the bench
+            out[key] = {"error": str(e)[:200]}
+    return out
 
 
 def serve_sweep(ss, args):
